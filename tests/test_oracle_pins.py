@@ -1,0 +1,297 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by the mathematics.
+
+Each test checks the oracle against something other than itself: dense inversion of Eq. (1)-(2),
+closed forms of the 1D tight-binding chain, channel counting, current conservation, the
+fluctuation-dissipation relation, the algebraic identity behind Eq. (6), and finite differences.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import make_device, chain_device, channel_device
+
+KT = O.KT_300K
+
+
+def _scatter(N, b, seed, gamma=0.05, f=0.7):
+    """Physical orbital-diagonal self-energies: Sigma^R = r - i g, Sigma^< = i f 2 g."""
+    rng = np.random.default_rng(seed)
+    g = gamma * rng.random((N, b))
+    r = 0.02 * rng.normal(size=(N, b))
+    sR = r - 1j * g
+    sL = 1j * f * 2 * g
+    return sR, sL
+
+
+def _blocks(M, N, b):
+    diag = [M[i * b:(i + 1) * b, i * b:(i + 1) * b] for i in range(N)]
+    lower = [M[(i + 1) * b:(i + 2) * b, i * b:(i + 1) * b] for i in range(N - 1)]
+    return diag, lower
+
+
+@pytest.mark.parametrize("N,b", [(1, 3), (2, 1), (3, 4), (6, 5)])
+@pytest.mark.parametrize("scatter", [False, True])
+def test_rgf_equals_dense_inverse(N, b, scatter):
+    dev = make_device(N, b, 11 + N * b)
+    V = np.random.default_rng(5).uniform(-0.3, 0.3, (N, b))
+    E, eta = 0.37, 1e-6
+    leads = O.lead_self_energies(dev.D, dev.T, E, eta, 0.1, -0.1, KT)
+    sR, sL = _scatter(N, b, 3) if scatter else (None, None)
+    r = O.rgf(dev.D, dev.T, E, eta, V, leads, sR, sL)
+    G, GL = O.dense_green(dev.D, dev.T, E, eta, V, leads, sR, sL)
+    Gd, _ = _blocks(G, N, b)
+    GLd, GLl = _blocks(GL, N, b)
+    scale = max(np.abs(G).max(), 1.0)
+    scale_l = max(np.abs(GL).max(), 1e-300)
+    for i in range(N):
+        assert np.abs(r["G"][i] - Gd[i]).max() < 1e-11 * scale
+        assert np.abs(r["GL"][i] - GLd[i]).max() < 1e-11 * scale_l
+    for i in range(N - 1):
+        assert np.abs(r["GLoff"][i] - GLl[i]).max() < 1e-11 * scale_l
+
+
+def _chain_surface_closed_form(z, eps, t):
+    disc = np.sqrt((z - eps) ** 2 - 4 * t * t + 0j)
+    roots = [((z - eps) + disc) / (2 * t * t), ((z - eps) - disc) / (2 * t * t)]
+    # the retarded surface Green's function is the root with |t g| < 1 (decaying into the lead)
+    return min(roots, key=lambda g: abs(t * g))
+
+
+@pytest.mark.parametrize("E", [-2.7, -1.3, -0.41, 0.2, 0.93, 1.999, 2.4])
+def test_sancho_rubio_chain_closed_form(E):
+    eps, t, eta = 0.0, 1.0, 1e-9
+    z = E + 1j * eta
+    gs, it, conv = O.sancho_rubio(np.array([[eps]]), np.array([[t]]), z)
+    assert conv and it < 100
+    exact = _chain_surface_closed_form(z, eps, t)
+    assert abs(gs[0, 0] - exact) < 2e-6 * max(1.0, abs(exact))
+    assert gs[0, 0].imag <= 1e-12
+
+
+def test_sancho_rubio_fixed_point_and_causality():
+    rng = np.random.default_rng(7)
+    b = 6
+    h = rng.normal(size=(b, b)) + 1j * rng.normal(size=(b, b))
+    h = 0.3 * (h + h.conj().T)
+    a = (rng.normal(size=(b, b)) + 1j * rng.normal(size=(b, b))) / np.sqrt(2 * b)
+    for E in [-1.1, 0.05, 0.8]:
+        z = E + 1j * 1e-6
+        gs, it, conv = O.sancho_rubio(h, a, z)
+        assert conv
+        resid = gs - np.linalg.inv(z * np.eye(b) - h - a @ gs @ a.conj().T)
+        assert np.abs(resid).max() < 1e-8 * max(1.0, np.abs(gs).max())
+        spec = np.linalg.eigvalsh(1j * (gs - gs.conj().T))
+        assert spec.min() > -1e-9 * max(1.0, np.abs(spec).max())
+
+
+def test_sancho_rubio_matches_long_finite_lead():
+    """With eta = 0.05 a lead of 3000 cells is indistinguishable from a semi-infinite one."""
+    rng = np.random.default_rng(8)
+    b = 3
+    h = rng.normal(size=(b, b)) + 1j * rng.normal(size=(b, b))
+    h = 0.25 * (h + h.conj().T)
+    a = (rng.normal(size=(b, b)) + 1j * rng.normal(size=(b, b))) / np.sqrt(2 * b)
+    z = 0.3 + 0.05j
+    g = np.linalg.inv(z * np.eye(b) - h)
+    for _ in range(3000):
+        g = np.linalg.inv(z * np.eye(b) - h - a @ g @ a.conj().T)
+    gs, _, conv = O.sancho_rubio(h, a, z)
+    assert conv
+    assert np.abs(gs - g).max() < 1e-10 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("E", [-2.5, -1.7, -0.3, 0.6, 1.95, 2.2, 3.1])
+def test_transmission_chain_is_step(E):
+    ch = chain_device(7, 0.0, 1.0)
+    o = O.solve_point(ch.D, ch.T, E, 0.0, None, eta_lead=1e-9)
+    expected = 1.0 if abs(E) < 2.0 else 0.0
+    assert abs(o["transmission"] - expected) < 1e-6
+
+
+def test_transmission_channel_counting():
+    dev = channel_device(4, 5, 21)
+    d, t = dev.meta["d"], dev.meta["t"]
+    for E in np.linspace(-3.2, 3.2, 41):
+        dist = np.abs(np.abs(E - d) - 2 * t)
+        if dist.min() < 1e-3:
+            continue
+        count = int(np.sum(np.abs(E - d) < 2 * t))
+        o = O.solve_point(dev.D, dev.T, E, 0.0, None, eta_lead=1e-9)
+        assert abs(o["transmission"] - count) < 1e-5, (E, o["transmission"], count)
+
+
+def test_caroli_equals_gnn_formula():
+    dev = make_device(5, 4, 31)
+    for E in [-1.0, 0.1, 1.2]:
+        o = O.solve_point(dev.D, dev.T, E, 0.0, None, eta_lead=1e-7)
+        G, _ = O.dense_green(dev.D, dev.T, E, 0.0, None, o["leads"])
+        Tc = O.transmission_caroli_dense(G, o["leads"]["gamL"], o["leads"]["gamR"], 5, 4)
+        assert abs(Tc - o["transmission"]) < 1e-9 * max(1.0, Tc)
+
+
+def test_current_conservation_and_landauer():
+    dev = make_device(6, 4, 41)
+    V = np.random.default_rng(2).uniform(-0.2, 0.2, (6, 4))
+    for E in [-0.8, -0.05, 0.07, 0.9]:
+        o = O.solve_point(dev.D, dev.T, E, 0.0, V, eta_lead=1e-7, mu_L=0.1, mu_R=-0.1)
+        j = o["current"]
+        df = O.fermi(E, 0.1, KT) - O.fermi(E, -0.1, KT)
+        land = df * o["transmission"]
+        assert np.abs(j - land).max() < 1e-9 * max(abs(land), 1e-12) + 1e-13
+        assert land >= -1e-15  # positive for left-to-right flow (mu_L > mu_R)
+        o0 = O.solve_point(dev.D, dev.T, E, 0.0, V, eta_lead=1e-7, mu_L=0.05, mu_R=0.05)
+        assert np.abs(o0["current"]).max() < 1e-12
+
+
+def test_fluctuation_dissipation_equilibrium():
+    N, b = 5, 4
+    dev = make_device(N, b, 51)
+    mu = 0.02
+    for E in [-0.5, 0.03, 0.4]:
+        f = float(O.fermi(E, mu, KT))
+        # equilibrium elastic scattering: Sigma^< = -f (Sigma^R - Sigma^A)
+        rng = np.random.default_rng(3)
+        gam = 0.03 * rng.random((N, b))
+        sR = 0.01 * rng.normal(size=(N, b)) - 1j * gam
+        sL = 1j * f * 2 * gam
+        # eta only in the leads: a device eta would broaden A without feeding Sigma^<
+        o = O.solve_point(dev.D, dev.T, E, 0.0, None, eta_lead=1e-6, mu_L=mu, mu_R=mu, sR=sR,
+                          sL=sL)
+        for Gi, GLi in zip(o["blocks"]["G"], o["blocks"]["GL"]):
+            ref = -f * (Gi - Gi.conj().T)
+            assert np.abs(GLi - ref).max() < 1e-9 * max(np.abs(ref).max(), 1e-12)
+
+
+def test_spectral_function_hermitian_psd_and_lesser_antihermitian():
+    N, b = 6, 5
+    dev = make_device(N, b, 61)
+    sR, sL = _scatter(N, b, 9)
+    for E in [-1.3, 0.0123, 0.77]:
+        o = O.solve_point(dev.D, dev.T, E, 1e-6, None, sR=sR, sL=sL)
+        for Gi, GLi in zip(o["blocks"]["G"], o["blocks"]["GL"]):
+            A = 1j * (Gi - Gi.conj().T)
+            assert np.abs(A - A.conj().T).max() == 0.0 or np.abs(A - A.conj().T).max() < 1e-14
+            w = np.linalg.eigvalsh(A)
+            assert w.min() > -1e-12 * np.abs(w).max()
+            assert np.abs(GLi + GLi.conj().T).max() < 1e-12 * max(np.abs(GLi).max(), 1e-300)
+        assert o["density"].min() > -1e-14
+
+
+def test_bose_occupation_at_300K():
+    # n0 = 1/(exp(hw/kT) - 1) for hw = 60 meV, kT = 25.852 meV is 0.10887 (closed form)
+    assert abs(O.bose(0.060, KT) - 1.0 / (np.exp(0.060 / KT) - 1.0)) < 1e-15
+    assert abs(O.bose(0.060, KT) - 0.108869) < 1e-5
+
+
+def test_scba_reduces_to_ballistic_and_truncates():
+    rng = np.random.default_rng(4)
+    n_k, n_E, n_orb = 3, 30, 7
+    dGR = rng.normal(size=(n_k, n_E, n_orb)) + 1j * rng.normal(size=(n_k, n_E, n_orb))
+    dGL = 1j * rng.random((n_k, n_E, n_orb))
+    wk = np.full(n_k, 1.0 / n_k)
+    sR, sL = O.scba_selfenergy(dGR, dGL, wk, 0.0, 0.0, 12, 0.1)
+    assert np.all(sR == 0) and np.all(sL == 0)
+    # a single nonzero energy j0 feeds the optical terms only at j0 +- shift
+    dGR[:] = 0
+    dGL[:] = 0
+    j0, sh = 15, 4
+    dGR[:, j0, :] = 1.0 + 2.0j
+    dGL[:, j0, :] = 3.0j
+    sR, sL = O.scba_selfenergy(dGR, dGL, wk, 0.0, 0.5, sh, 0.25)
+    nz_R = sorted(set(np.nonzero(np.abs(sR).max(axis=1))[0].tolist()))
+    nz_L = sorted(set(np.nonzero(np.abs(sL).max(axis=1))[0].tolist()))
+    assert nz_R == [j0 - sh, j0 + sh] and nz_L == [j0 - sh, j0 + sh]
+    # emission (E -> E - hw) carries 1 + n0, absorption carries n0 (Eq. 5)
+    assert np.allclose(sL[j0 - sh], 0.5 * 1.25 * 3.0j)
+    assert np.allclose(sL[j0 + sh], 0.5 * 0.25 * 3.0j)
+    # energies shifted off the grid contribute nothing
+    dGL[:] = 0
+    dGL[:, 1, :] = 1j
+    sR, sL = O.scba_selfenergy(dGR * 0, dGL, wk, 0.0, 1.0, 5, 0.1)
+    assert np.abs(sL[0]).max() == 0.0 and np.abs(sL[6]).max() > 0
+
+
+def test_scba_retarded_antihermitian_part_is_half_greater_minus_lesser():
+    """Eq. (6) (comma read as '+') has anti-Hermitian part (Sigma^> - Sigma^<) / 2 exactly.
+
+    Built independently: G^> = G^R - G^A + G^<, and Sigma^> of the optical phonon takes
+    (1+n0) G^>(E-hw) + n0 G^>(E+hw); the acoustic one D_ac G^>(E).
+    """
+    rng = np.random.default_rng(12)
+    n_k, n_E, n_orb, sh = 2, 40, 5, 6
+    n0, Dac, Dop = 0.1089, 0.01, 0.02
+    gam = rng.random((n_k, n_E, n_orb))
+    f = rng.random((n_k, n_E, n_orb))
+    dGR = 0.3 * rng.normal(size=gam.shape) - 1j * gam       # diag G^R
+    dGL = 1j * f * 2 * gam                                    # diag G^< = i f A
+    dGG = dGR - dGR.conj() + dGL                               # diag G^>
+    wk = np.array([0.3, 0.7])
+    sR, sL = O.scba_selfenergy(dGR, dGL, wk, Dac, Dop, sh, n0)
+    sumG = np.einsum("k,kej->ej", wk, dGG)
+    sumL = np.einsum("k,kej->ej", wk, dGL)
+
+    def at(a, j):
+        return a[j] if 0 <= j < n_E else 0 * a[0]
+
+    for j in range(n_E):
+        sG = Dac * sumG[j] + Dop * ((1 + n0) * at(sumG, j - sh) + n0 * at(sumG, j + sh))
+        sLj = Dac * sumL[j] + Dop * ((1 + n0) * at(sumL, j + sh) + n0 * at(sumL, j - sh))
+        anti = 0.5 * (sR[j] - sR[j].conj())
+        assert np.allclose(anti, 0.5 * (sG - sLj), atol=1e-14)
+        assert np.allclose(sL[j], sLj, atol=1e-14)
+
+
+def test_gradient_dense_matches_finite_differences():
+    N, b = 3, 3
+    dev = make_device(N, b, 71)
+    rng = np.random.default_rng(6)
+    V = rng.uniform(-0.2, 0.2, (N, b))
+    c = rng.normal(size=(N * b))
+    d = rng.normal(size=(N - 1))
+    E, eta = 0.21, 1e-3
+    leads = O.lead_self_energies(dev.D, dev.T, E, eta, 0.1, -0.1, KT)
+
+    def loss(Vx):
+        r = O.rgf(dev.D, dev.T, E, eta, Vx, leads)
+        return float(c @ O.density_from_blocks(r["GL"]) + d @ O.current_from_blocks(dev.T, r["GLoff"]))
+
+    g = O.gradient_dense(dev.D, dev.T, E, eta, V, leads, c, d)
+    h = 1e-5
+    fd = np.zeros_like(V)
+    for i in range(N):
+        for j in range(b):
+            Vp = V.copy()
+            Vm = V.copy()
+            Vp[i, j] += h
+            Vm[i, j] -= h
+            fd[i, j] = (loss(Vp) - loss(Vm)) / (2 * h)
+    assert np.abs(g - fd).max() < 1e-6 * np.abs(fd).max()
+
+
+def test_acoustic_scba_conserves_current_per_energy():
+    """Elastic (acoustic) scattering conserves the bond current at every energy at convergence.
+
+    Clean channels with every channel open keep all states coupled to the leads, so the Born
+    iteration converges with no device eta (a device eta would leak current).
+    """
+    N, b = 5, 3
+    dev = channel_device(N, b, 21)
+    E = np.linspace(-0.2, 0.2, 5)
+    assert all(np.all(np.abs(e - dev.meta["d"]) < 2 * dev.meta["t"]) for e in E)
+    sR = np.zeros((len(E), N * b), dtype=complex)
+    sL = np.zeros_like(sR)
+    for _ in range(200):
+        outs = [O.solve_point(dev.D, dev.T, e, 0.0, None, eta_lead=1e-7, sR=sR[i].reshape(N, b),
+                              sL=sL[i].reshape(N, b)) for i, e in enumerate(E)]
+        dGR = np.array([o["diagGR"] for o in outs])[None]
+        dGL = np.array([o["diagGL"] for o in outs])[None]
+        sR, sL, delta = O.scba_step(dGR, dGL, np.ones(1), 0.05, 0.0, 3, 0.1, sR, sL)
+        if delta < 1e-14:
+            break
+    assert delta < 1e-12
+    for o in outs:
+        j = o["current"]
+        assert np.abs(j - j.mean()).max() < 1e-9 * max(np.abs(j).max(), 1e-12)
+    # scattering changes the current relative to the ballistic Landauer value
+    o_b = O.solve_point(dev.D, dev.T, E[2], 0.0, None, eta_lead=1e-7)
+    assert abs(outs[2]["current"][0] - o_b["current"][0]) > 1e-6 * abs(o_b["current"][0])
