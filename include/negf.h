@@ -1,0 +1,208 @@
+/*
+ * negf.h -- C ABI of the GB300 recursive Green's function (RGF) library.
+ *
+ * The library solves, for many independent (energy E, transverse momentum k, alloy sample)
+ * points, the nonequilibrium Green's function equations of a block-tridiagonal device
+ * Hamiltonian (NEMO5 paper, Eqs. 1-8):
+ *
+ *   G^R(k,E) = (E - H(k) - e Phi - Sigma^R(k,E))^-1                        (Eq. 1)
+ *   G^<(k,E) = G^R Sigma^< G^R^H                                          (Eq. 2)
+ *   Sigma    = Sigma_lead + Sigma_optical + Sigma_acoustic                   (Eq. 3)
+ *   Sigma_acoustic, Sigma_optical from diag G at E and E +- hbar omega      (Eqs. 4-6)
+ *   density and current integrands                                          (Eqs. 7-8)
+ *
+ * Only the diagonal and first off-diagonal blocks of G^R and G^< are formed (recursive
+ * Green's function sweeps).  Lead self-energies come from Sancho-Rubio decimation of
+ * semi-infinite periodic copies of the end slabs.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  - Complex numbers are interleaved {double re, double im} (the layout of torch.complex128
+ *    and C99 double complex).  Every b x b block is row-major and contiguous.
+ *  - Every array argument is a DEVICE pointer owned by the caller, unless its comment says
+ *    "host".  The library never frees or keeps caller memory after a call returns.
+ *  - Temporary device memory is the caller's workspace (`ws`, `ws_bytes`), sized by
+ *    negf_workspace_size().  The library allocates no device memory of its own.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *    Outputs are valid after the stream is synchronised.  Several points are solved
+ *    concurrently; the workspace holds a chunk of them at a time.
+ *  - Return value: NEGF_OK, or an error detected on the host before any launch
+ *    (NEGF_ERR_ARG, NEGF_ERR_NOMEM, NEGF_ERR_UNSUPPORTED) or a CUDA launch error
+ *    (NEGF_ERR_CUDA).  Numerical trouble of single points is reported per point in
+ *    `status[n_pts]` (bit set of NEGF_PT_*), written on the device; the call itself still
+ *    returns NEGF_OK.  No exception crosses the ABI and no kernel traps.
+ *  - Units: energies and potentials in eV.  Slab i (0-based) owns orbitals i*b .. i*b+b-1.
+ */
+#ifndef NEGF_H_
+#define NEGF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NEGF_ABI_VERSION 1
+
+typedef enum {
+  NEGF_OK = 0,
+  NEGF_ERR_ARG = 1,           /* invalid argument (null pointer, bad size, bad option)    */
+  NEGF_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed               */
+  NEGF_ERR_NOMEM = 3,         /* workspace smaller than negf_workspace_size() asks for     */
+  NEGF_ERR_NOT_CONVERGED = 4, /* (per-point status summary) decimation did not converge   */
+  NEGF_ERR_SINGULAR = 5,      /* (per-point status summary) a zero pivot was met           */
+  NEGF_ERR_NONFINITE = 6,     /* (per-point status summary) NaN or Inf in an output        */
+  NEGF_ERR_TIMEOUT = 7,       /* a bounded device wait gave up                             */
+  NEGF_ERR_UNSUPPORTED = 8    /* option or size not supported by this build                */
+} negf_status;
+
+/* Per-point status bits written to `status[p]`. */
+#define NEGF_PT_OK 0
+#define NEGF_PT_NOT_CONVERGED 1 /* Sancho-Rubio reached sr_max_iter without converging      */
+#define NEGF_PT_SINGULAR 2      /* a pivot of a block inverse was exactly zero               */
+#define NEGF_PT_NONFINITE 4     /* an output of this point is NaN or Inf                    */
+#define NEGF_PT_BAD_INDEX 8     /* sys_idx / e_idx out of range: the point was clamped to a
+                                   valid row and its results are meaningless               */
+
+typedef enum {
+  NEGF_PREC_FP64 = 0,  /* every block operation in FP64 on the CUDA cores (reference form) */
+  NEGF_PREC_MIXED = 1  /* block GEMMs on the tensor cores as exact split-BF16 slices with
+                          FP32 accumulation, FP64 storage, pivoting, norms and reductions  */
+} negf_precision;
+
+/* Block-tridiagonal device Hamiltonians H(k) of n_sys systems (transverse k x alloy sample).
+ * H_diag[s][i]  = H_ii        (Hermitian b x b),  s < n_sys, i < n_slabs
+ * H_up[s][i]    = H_{i,i+1}   (b x b),            i < n_slabs - 1;  H_{i+1,i} = H_up^H.
+ * The left lead is the periodic continuation of slab 0 (cell H_00, hopping H_01), the
+ * right lead that of slab N-1 (cell H_{N-1,N-1}, hopping H_{N-2,N-1}). */
+typedef struct {
+  int32_t n_sys;
+  int32_t n_slabs;       /* N >= 1; N == 1 has no hopping and flat leads (Sigma_lead = 0) */
+  int32_t block;         /* b >= 1 */
+  int32_t reserved;
+  const double* H_diag;  /* device, complex128 [n_sys][N][b][b] */
+  const double* H_up;    /* device, complex128 [n_sys][N-1][b][b]; may be NULL when N == 1 */
+} negf_device;
+
+typedef struct {
+  double eta_lead;       /* imaginary part of z = E + i eta in the lead decimation (eV)   */
+  double eta_device;     /* imaginary part of z in the device (eV), >= 0                   */
+  double mu_L, mu_R;     /* Fermi levels of the left / right contact (eV)                  */
+  double kT;             /* contact temperature (eV)                                        */
+  double sr_tol;         /* decimation stop: max(|alpha|_max,|beta|_max) <
+                            sr_tol * max(|h|_max, |tau|_max) (default 1e-13)                 */
+  int32_t sr_max_iter;   /* decimation iteration cap (default 100)                          */
+  int32_t precision;     /* negf_precision                                                  */
+  int32_t refine_steps;  /* mixed precision: Newton-Schulz steps X <- X + X (I - M X) after
+                            each block inverse (default 2)                                  */
+  int32_t chunk;         /* points solved concurrently (0 = library default)                */
+} negf_options;
+
+/* Fill `opt` with the defaults (eta 1e-6 in leads and device, mu_L = +0.1, mu_R = -0.1,
+ * kT = 0.025852, sr_tol = 1e-13, sr_max_iter = 100, FP64, refine_steps = 2, chunk = 0). */
+void negf_default_options(negf_options* opt);
+
+int32_t negf_abi_version(void);
+const char* negf_status_string(negf_status s);
+
+/* Which call a workspace is sized for. */
+#define NEGF_WS_LEAD 0
+#define NEGF_WS_RGF 1
+#define NEGF_WS_ADJOINT 2
+
+/* Bytes of device workspace a call of kind `which` needs for n_pts points (the library
+ * works through the points `opt->chunk` at a time, so the size saturates). */
+size_t negf_workspace_size(const negf_device* dev, int32_t n_pts, const negf_options* opt,
+                           int32_t which);
+
+/* Lead self-energies (Eq. 3, Sigma_lead) by Sancho-Rubio decimation (Lopez Sancho, Lopez
+ * Sancho & Rubio, J. Phys. F 15, 851 (1985)); the paper's own leads use the transfer matrix
+ * or complex absorbing potential methods (text below Eq. 6), which reach the same unique
+ * retarded surface Green's function.
+ *   E[n_pts]        device double: energy of each point
+ *   sys_idx[n_pts]  device int32:  which Hamiltonian of `dev` the point uses (0..n_sys-1)
+ *   sigma_R         device complex128 [n_pts][2][b][b] out: Sigma^R of side 0 = left lead
+ *                   (acts on slab 0: H_01^H g_L H_01) and side 1 = right lead (acts on
+ *                   slab N-1: H_{N-2,N-1} g_R H_{N-2,N-1}^H)
+ *   sigma_L         device complex128 [n_pts][2][b][b] out: Sigma^< = i f(E) Gamma,
+ *                   Gamma = i (Sigma^R - Sigma^R^H), f the contact's Fermi function
+ *   iters           device int32 [n_pts][2] out (nullable): decimation steps per side
+ *   status          device int32 [n_pts] out: NEGF_PT_* bits                            */
+negf_status negf_lead_selfenergy(const negf_device* dev, int32_t n_pts, const double* E,
+                                 const int32_t* sys_idx, const negf_options* opt,
+                                 double* sigma_R, double* sigma_L, int32_t* iters,
+                                 int32_t* status, void* ws, size_t ws_bytes, void* stream);
+
+/* One RGF solve per point: forward sweep of left-connected g^R, g^< and backward sweep for
+ * the diagonal blocks G^R_ii, G^<_ii and the off-diagonal G^<_{i+1,i} (Eqs. 1-2), then the
+ * observables.
+ *   V           device double [N][b] (nullable = 0): on-site potential (the e Phi of Eq. 1),
+ *               added to the diagonal of H_ii for every point
+ *   sigma_R/L   device complex128 [n_pts][2][b][b]: lead self-energies (negf_lead_selfenergy)
+ *   scat_R/L    device complex128 [n_rows][N*b] (nullable = ballistic): orbital-diagonal
+ *               phonon self-energies Sigma^R, Sigma^< of Eqs. 4-6; point p uses row
+ *               e_idx[p] (e_idx nullable = row p, and then n_rows must be >= n_pts)
+ *   density     device double [n_pts][N*b] out (nullable): n_j(E) = Im G^<_jj / (2 pi)
+ *   current     device double [n_pts][N-1] out (nullable): bond current
+ *               j_i(E) = 2 Re Tr[H_{i,i+1} G^<_{i+1,i}] (Eq. 8, per spin, units 1/h)
+ *   transmission device double [n_pts] out (nullable):
+ *               T(E) = Tr[Gamma_R A_NN] - Tr[Gamma_R G_NN Gamma_R G_NN^H]  (exact when
+ *               ballistic; with scattering it is the flux into the right lead per unit
+ *               occupation difference of all other sources)
+ *   diagGR/GL   device complex128 [n_pts][N*b] out (nullable): diag G^R, diag G^< for the
+ *               self-consistent Born step (negf_scba_step)
+ *   status      device int32 [n_pts] out                                                 */
+negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* E,
+                           const int32_t* sys_idx, const double* V, const double* sigma_R,
+                           const double* sigma_L, const double* scat_R, const double* scat_L,
+                           const int32_t* e_idx, int32_t n_rows, const negf_options* opt,
+                           double* density,
+                           double* current, double* transmission, double* diagGR,
+                           double* diagGL, int32_t* status, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/* One self-consistent Born update of the orbital-diagonal phonon self-energies (Eqs. 4-6):
+ *   Sigma_ac^{R,<}(E_j) = D_ac sum_k w_k dG^{R,<}(k, E_j)                                (4)
+ *   Sigma_op^<(E_j) = D_op sum_k w_k [(1+n0) dG^<(k,E_{j+s}) + n0 dG^<(k,E_{j-s})]       (5)
+ *   Sigma_op^R(E_j) = D_op sum_k w_k [(1+n0) dG^R(k,E_{j-s}) + n0 dG^R(k,E_{j+s})
+ *                                     + dG^<(k,E_{j-s})/2 - dG^<(k,E_{j+s})/2]           (6)
+ * (the printed comma inside Eq. 6 is read as '+'; hbar omega = `shift` grid steps; energies
+ * off the grid contribute zero; the prefactors of Eqs. 4-6 are D_ac, D_op in eV^2 and the k'
+ * integral is the weighted sum).  Then Sigma <- (1-mix) Sigma_old + mix Sigma_new.
+ *   w_k        device double [n_k]
+ *   diagGR/GL  device complex128 [n_k][n_E][n_orb]   (negf_rgf_solve's diag outputs with
+ *              points ordered k-major)
+ *   sigma_R/L  device complex128 [n_E][n_orb] in: old Sigma, out: new Sigma
+ *   delta_out  device double [1] out: max over entries of |Sigma_new - Sigma_old|        */
+negf_status negf_scba_step(int32_t n_k, int32_t n_E, int32_t n_orb, const double* w_k,
+                           double D_ac, double D_op, int32_t shift, double n0, double mix,
+                           const double* diagGR, const double* diagGL, double* sigma_R,
+                           double* sigma_L, double* delta_out, void* stream);
+
+/* Reverse-mode derivative of the observables of negf_rgf_solve with respect to the on-site
+ * potential V (the e Phi of Eq. 1), for a Newton-Poisson loop around Eq. 9.  With the
+ * same inputs as negf_rgf_solve (self-energies held fixed) and the cotangents
+ *   density_bar [n_pts][N*b] (nullable), current_bar [n_pts][N-1] (nullable),
+ * it accumulates V_bar[N][b] += sum_p sum_j density_bar[p][j] dn_j(p)/dV
+ *                                 + sum_i current_bar[p][i] dj_i(p)/dV.
+ * V_bar is device double [N][b] and is overwritten (not accumulated into).              */
+negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, const double* E,
+                             const int32_t* sys_idx, const double* V, const double* sigma_R,
+                             const double* sigma_L, const double* scat_R,
+                             const double* scat_L, const int32_t* e_idx, int32_t n_rows,
+                             const negf_options* opt, const double* density_bar,
+                             const double* current_bar, double* V_bar, int32_t* status,
+                             void* ws, size_t ws_bytes, void* stream);
+
+/* Energy / k quadrature of Eqs. 7-8 in FP64 in a fixed order (deterministic):
+ *   out[g][j] = sum over p with group[p] == g (in increasing p) of w[p] * in[p][j]
+ *   in [n_pts][len], w [n_pts], group [n_pts] (nullable = all in group 0), out [n_groups][len]
+ * All device pointers. */
+negf_status negf_integrate(int32_t n_pts, int32_t len, int32_t n_groups, const double* w,
+                           const int32_t* group, const double* in, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEGF_H_ */

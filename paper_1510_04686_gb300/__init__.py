@@ -1,0 +1,19 @@
+"""GB300 recursive Green's function library (NEGF hot path of NEMO5, arXiv:1510.04686).
+
+The numerical work runs in ``_lib/libnegf.so`` (CUDA, sm_103a), reached through its C ABI
+(``include/negf.h``).  This package only marshals torch tensors into that ABI.
+"""
+from .negf import (  # noqa: F401
+    NegfError,
+    Device,
+    options,
+    lead_selfenergy,
+    rgf_solve,
+    scba_step,
+    rgf_adjoint,
+    integrate,
+    workspace_size,
+    library,
+    PREC_FP64,
+    PREC_MIXED,
+)

@@ -1,0 +1,272 @@
+"""ctypes binding of the C ABI in include/negf.h.
+
+Argument marshalling only: tensors must already live on the GPU with the documented dtype and
+layout; every computation happens in libnegf.so.  A missing library raises, there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int32, c_size_t, c_void_p
+
+import torch
+
+from . import _build
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+WS_LEAD, WS_RGF, WS_ADJOINT = 0, 1, 2
+
+_STATUS = {
+    0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "workspace too small",
+    4: "lead decimation did not converge", 5: "zero pivot", 6: "non-finite output",
+    7: "timeout", 8: "unsupported option or size",
+}
+
+
+class NegfError(RuntimeError):
+    def __init__(self, code, where):
+        super().__init__(f"{where}: negf status {code} ({_STATUS.get(code, 'unknown')})")
+        self.code = code
+
+
+class _Dev(ctypes.Structure):
+    _fields_ = [("n_sys", c_int32), ("n_slabs", c_int32), ("block", c_int32),
+                ("reserved", c_int32), ("H_diag", c_void_p), ("H_up", c_void_p)]
+
+
+class _Opt(ctypes.Structure):
+    _fields_ = [("eta_lead", c_double), ("eta_device", c_double), ("mu_L", c_double),
+                ("mu_R", c_double), ("kT", c_double), ("sr_tol", c_double),
+                ("sr_max_iter", c_int32), ("precision", c_int32), ("refine_steps", c_int32),
+                ("chunk", c_int32)]
+
+
+_LIB = None
+EXPORTS = ("negf_default_options", "negf_abi_version", "negf_status_string",
+           "negf_workspace_size", "negf_lead_selfenergy", "negf_rgf_solve", "negf_scba_step",
+           "negf_rgf_adjoint", "negf_integrate")
+
+
+def library():
+    """Load libnegf.so (built in-tree by __graft_entry__.build / _build.build)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnegf.so not found at {path}; build it with "
+                           "paper_1510_04686_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    P = c_void_p
+    lib.negf_default_options.argtypes = [POINTER(_Opt)]
+    lib.negf_default_options.restype = None
+    lib.negf_abi_version.restype = c_int32
+    lib.negf_status_string.argtypes = [c_int32]
+    lib.negf_status_string.restype = ctypes.c_char_p
+    lib.negf_workspace_size.argtypes = [POINTER(_Dev), c_int32, POINTER(_Opt), c_int32]
+    lib.negf_workspace_size.restype = c_size_t
+    lib.negf_lead_selfenergy.argtypes = [POINTER(_Dev), c_int32, P, P, POINTER(_Opt), P, P, P, P,
+                                         P, c_size_t, P]
+    lib.negf_lead_selfenergy.restype = c_int32
+    lib.negf_rgf_solve.argtypes = [POINTER(_Dev), c_int32, P, P, P, P, P, P, P, P, c_int32,
+                                   POINTER(_Opt), P, P, P, P, P, P, P, c_size_t, P]
+    lib.negf_rgf_solve.restype = c_int32
+    lib.negf_scba_step.argtypes = [c_int32, c_int32, c_int32, P, c_double, c_double, c_int32,
+                                   c_double, c_double, P, P, P, P, P, P]
+    lib.negf_scba_step.restype = c_int32
+    lib.negf_rgf_adjoint.argtypes = [POINTER(_Dev), c_int32, P, P, P, P, P, P, P, P, c_int32,
+                                     POINTER(_Opt), P, P, P, P, P, c_size_t, P]
+    lib.negf_rgf_adjoint.restype = c_int32
+    lib.negf_integrate.argtypes = [c_int32, c_int32, c_int32, P, P, P, P, P]
+    lib.negf_integrate.restype = c_int32
+    _LIB = lib
+    return lib
+
+
+def options(**kw) -> _Opt:
+    """negf_options with the library defaults, overridden by keyword."""
+    o = _Opt()
+    library().negf_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return None if t is None else c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, name, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _rows(scat):
+    return 0 if scat is None else int(scat.shape[0])
+
+
+def _stream():
+    return c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Device:
+    """Block-tridiagonal Hamiltonians H_diag [n_sys,N,b,b], H_up [n_sys,N-1,b,b] (complex128)."""
+
+    def __init__(self, H_diag: torch.Tensor, H_up: torch.Tensor | None):
+        _need(H_diag, torch.complex128, "H_diag")
+        if H_diag.dim() != 4 or H_diag.shape[2] != H_diag.shape[3]:
+            raise ValueError("H_diag must be [n_sys, N, b, b]")
+        n_sys, N, b, _ = H_diag.shape
+        if N > 1:
+            _need(H_up, torch.complex128, "H_up", (n_sys, N - 1, b, b))
+        self.H_diag, self.H_up = H_diag, H_up
+        self.n_sys, self.N, self.b = int(n_sys), int(N), int(b)
+        self.c = _Dev(self.n_sys, self.N, self.b, 0, H_diag.data_ptr(),
+                      H_up.data_ptr() if (H_up is not None and N > 1) else None)
+
+
+_WS = {}
+
+
+def _workspace(nbytes, device):
+    key = (str(device),)
+    buf = _WS.get(key)
+    if buf is None or buf.numel() < nbytes:
+        _WS.pop(key, None)
+        buf = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+        _WS[key] = buf
+    return buf
+
+
+def workspace_size(dev: Device, n_pts: int, opt: _Opt, which: int) -> int:
+    return int(library().negf_workspace_size(ctypes.byref(dev.c), n_pts, ctypes.byref(opt), which))
+
+
+def _check(code, where):
+    if code != 0:
+        raise NegfError(code, where)
+
+
+def lead_selfenergy(dev: Device, E: torch.Tensor, sys_idx: torch.Tensor, opt: _Opt):
+    """Sancho-Rubio lead self-energies: returns dict(sigma_R, sigma_L [n,2,b,b], iters, status)."""
+    _need(E, torch.float64, "E")
+    n = E.numel()
+    _need(sys_idx, torch.int32, "sys_idx", (n,))
+    b = dev.b
+    dv = E.device
+    sR = torch.empty((n, 2, b, b), dtype=torch.complex128, device=dv)
+    sL = torch.empty_like(sR)
+    it = torch.empty((n, 2), dtype=torch.int32, device=dv)
+    st = torch.empty((n,), dtype=torch.int32, device=dv)
+    nb = workspace_size(dev, max(n, 1), opt, WS_LEAD)
+    ws = _workspace(nb, dv)
+    _check(library().negf_lead_selfenergy(ctypes.byref(dev.c), n, _ptr(E), _ptr(sys_idx),
+                                          ctypes.byref(opt), _ptr(sR), _ptr(sL), _ptr(it),
+                                          _ptr(st), _ptr(ws), nb, _stream()),
+           "negf_lead_selfenergy")
+    return dict(sigma_R=sR, sigma_L=sL, iters=it, status=st)
+
+
+def rgf_solve(dev: Device, E, sys_idx, sigma_R, sigma_L, opt, V=None, scat_R=None, scat_L=None,
+              e_idx=None, outputs=("density", "current", "transmission"), diag=False):
+    """Forward/backward RGF sweeps and observables for every point (negf_rgf_solve)."""
+    _need(E, torch.float64, "E")
+    n = E.numel()
+    N, b = dev.N, dev.b
+    _need(sys_idx, torch.int32, "sys_idx", (n,))
+    _need(sigma_R, torch.complex128, "sigma_R", (n, 2, b, b))
+    _need(sigma_L, torch.complex128, "sigma_L", (n, 2, b, b))
+    if V is not None:
+        _need(V, torch.float64, "V", (N, b))
+    if scat_R is not None:
+        _need(scat_R, torch.complex128, "scat_R")
+        _need(scat_L, torch.complex128, "scat_L", tuple(scat_R.shape))
+    if e_idx is not None:
+        _need(e_idx, torch.int32, "e_idx", (n,))
+    dv = E.device
+    out = {}
+    dens = torch.empty((n, N * b), dtype=torch.float64, device=dv) if "density" in outputs else None
+    cur = (torch.empty((n, max(N - 1, 0)), dtype=torch.float64, device=dv)
+           if "current" in outputs else None)
+    tr = torch.empty((n,), dtype=torch.float64, device=dv) if "transmission" in outputs else None
+    dGR = torch.empty((n, N * b), dtype=torch.complex128, device=dv) if diag else None
+    dGL = torch.empty((n, N * b), dtype=torch.complex128, device=dv) if diag else None
+    st = torch.empty((n,), dtype=torch.int32, device=dv)
+    nb = workspace_size(dev, max(n, 1), opt, WS_RGF)
+    ws = _workspace(nb, dv)
+    _check(library().negf_rgf_solve(ctypes.byref(dev.c), n, _ptr(E), _ptr(sys_idx), _ptr(V),
+                                    _ptr(sigma_R), _ptr(sigma_L), _ptr(scat_R), _ptr(scat_L),
+                                    _ptr(e_idx), _rows(scat_R), ctypes.byref(opt), _ptr(dens),
+                                    _ptr(cur),
+                                    _ptr(tr), _ptr(dGR), _ptr(dGL), _ptr(st), _ptr(ws), nb,
+                                    _stream()), "negf_rgf_solve")
+    out.update(density=dens, current=cur, transmission=tr, diagGR=dGR, diagGL=dGL, status=st)
+    return out
+
+
+def scba_step(diagGR, diagGL, w_k, sigma_R, sigma_L, D_ac, D_op, shift, n0, mix=1.0):
+    """One Born update (negf_scba_step); sigma_R/L [n_E, n_orb] are updated in place.
+
+    diagGR/diagGL are [n_k, n_E, n_orb] complex128; returns the device scalar max|dSigma|."""
+    _need(diagGR, torch.complex128, "diagGR")
+    n_k, n_E, n_orb = diagGR.shape
+    _need(diagGL, torch.complex128, "diagGL", (n_k, n_E, n_orb))
+    _need(w_k, torch.float64, "w_k", (n_k,))
+    _need(sigma_R, torch.complex128, "sigma_R", (n_E, n_orb))
+    _need(sigma_L, torch.complex128, "sigma_L", (n_E, n_orb))
+    delta = torch.empty((1,), dtype=torch.float64, device=diagGR.device)
+    _check(library().negf_scba_step(n_k, n_E, n_orb, _ptr(w_k), float(D_ac), float(D_op),
+                                    int(shift), float(n0), float(mix), _ptr(diagGR),
+                                    _ptr(diagGL), _ptr(sigma_R), _ptr(sigma_L), _ptr(delta),
+                                    _stream()), "negf_scba_step")
+    return delta
+
+
+def rgf_adjoint(dev: Device, E, sys_idx, sigma_R, sigma_L, opt, density_bar=None,
+                current_bar=None, V=None, scat_R=None, scat_L=None, e_idx=None):
+    """dL/dV for cotangents of density [n, N*b] and current [n, N-1] (negf_rgf_adjoint)."""
+    _need(E, torch.float64, "E")
+    n = E.numel()
+    N, b = dev.N, dev.b
+    if density_bar is not None:
+        _need(density_bar, torch.float64, "density_bar", (n, N * b))
+    if current_bar is not None:
+        _need(current_bar, torch.float64, "current_bar", (n, N - 1))
+    if V is not None:
+        _need(V, torch.float64, "V", (N, b))
+    dv = E.device
+    Vbar = torch.empty((N, b), dtype=torch.float64, device=dv)
+    st = torch.empty((n,), dtype=torch.int32, device=dv)
+    nb = workspace_size(dev, max(n, 1), opt, WS_ADJOINT)
+    ws = _workspace(nb, dv)
+    _check(library().negf_rgf_adjoint(ctypes.byref(dev.c), n, _ptr(E), _ptr(sys_idx), _ptr(V),
+                                      _ptr(sigma_R), _ptr(sigma_L), _ptr(scat_R), _ptr(scat_L),
+                                      _ptr(e_idx), _rows(scat_R), ctypes.byref(opt),
+                                      _ptr(density_bar),
+                                      _ptr(current_bar), _ptr(Vbar), _ptr(st), _ptr(ws), nb,
+                                      _stream()), "negf_rgf_adjoint")
+    return Vbar, st
+
+
+def integrate(values, w, group=None, n_groups=1):
+    """out[g] = sum_{p in g} w[p] values[p] in FP64, fixed order (negf_integrate)."""
+    _need(values, torch.float64, "values")
+    n = values.shape[0]
+    ln = values[0].numel() if n else 0
+    _need(w, torch.float64, "w", (n,))
+    out = torch.empty((n_groups,) + tuple(values.shape[1:]), dtype=torch.float64,
+                      device=values.device)
+    _check(library().negf_integrate(n, ln, n_groups, _ptr(w), _ptr(group), _ptr(values),
+                                    _ptr(out), _stream()), "negf_integrate")
+    return out

@@ -1,0 +1,106 @@
+"""Host-side checks of the C ABI: the library loads, exports every declared symbol, and rejects
+bad arguments before any CUDA call (so these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1510_04686_gb300 as negf
+from paper_1510_04686_gb300 import negf as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    negf._build.build()
+    return negf.library()
+
+
+def _declared():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            names |= set(re.findall(r"^\s*[\w\s\*]*?\b(negf_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"negf_rgf_solve", "negf_lead_selfenergy", "negf_scba_step", "negf_rgf_adjoint"} <= names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_defaults_and_strings(lib):
+    assert lib.negf_abi_version() == 1
+    o = negf.options()
+    assert o.eta_lead == 1e-6 and o.eta_device == 1e-6 and o.sr_max_iter == 100
+    assert o.precision == negf.PREC_FP64 and o.refine_steps == 2
+    for code in range(9):
+        assert lib.negf_status_string(code)
+    assert lib.negf_status_string(99) == b"unknown status"
+
+
+def _dev(n_sys=1, N=4, b=8, hd=1, hu=1):
+    return B._Dev(n_sys, N, b, 0, hd, hu)
+
+
+def test_workspace_size_validation(lib):
+    o = negf.options()
+    d = _dev()
+    for which in (B.WS_LEAD, B.WS_RGF):
+        assert lib.negf_workspace_size(ctypes.byref(d), 10, ctypes.byref(o), which) > 0
+    assert lib.negf_workspace_size(ctypes.byref(_dev(N=0)), 10, ctypes.byref(o), B.WS_RGF) == 0
+    assert lib.negf_workspace_size(ctypes.byref(d), 0, ctypes.byref(o), B.WS_RGF) == 0
+    bad = negf.options(precision=7)
+    assert lib.negf_workspace_size(ctypes.byref(d), 10, ctypes.byref(bad), B.WS_RGF) == 0
+    # the size saturates with the chunk
+    o2 = negf.options(chunk=4)
+    s4 = lib.negf_workspace_size(ctypes.byref(d), 4, ctypes.byref(o2), B.WS_RGF)
+    s100 = lib.negf_workspace_size(ctypes.byref(d), 100, ctypes.byref(o2), B.WS_RGF)
+    assert s4 == s100
+
+
+def test_bad_arguments_rejected_on_host(lib):
+    o = negf.options()
+    P = ctypes.c_void_p
+    fake = P(16)
+    d = _dev()
+    # missing H_up with N > 1
+    r = lib.negf_rgf_solve(ctypes.byref(_dev(hu=0)), 3, fake, fake, None, fake, fake, None, None,
+                           None, 0, ctypes.byref(o), None, None, None, None, None, fake, fake, 1 << 30,
+                           None)
+    assert r == 1
+    # scat_R without scat_L
+    r = lib.negf_rgf_solve(ctypes.byref(d), 3, fake, fake, None, fake, fake, fake, None, None,
+                           1, ctypes.byref(o), None, None, None, None, None, fake, fake, 1 << 30, None)
+    assert r == 1
+    # workspace too small
+    r = lib.negf_rgf_solve(ctypes.byref(d), 3, fake, fake, None, fake, fake, None, None, None,
+                           0, ctypes.byref(o), None, None, None, None, None, fake, fake, 16, None)
+    assert r == 3
+    # bad options
+    bad = negf.options(kT=0.0)
+    r = lib.negf_lead_selfenergy(ctypes.byref(d), 3, fake, fake, ctypes.byref(bad), fake, fake,
+                                 None, fake, fake, 1 << 30, None)
+    assert r == 1
+    r = lib.negf_scba_step(0, 4, 4, fake, 0.01, 0.01, 1, 0.1, 1.0, fake, fake, fake, fake, fake,
+                           None)
+    assert r == 1
+    r = lib.negf_scba_step(1, 4, 4, fake, 0.01, 0.01, 1, 0.1, 0.0, fake, fake, fake, fake, fake,
+                           None)
+    assert r == 1
+    # zero points is a no-op
+    r = lib.negf_rgf_solve(ctypes.byref(d), 0, None, None, None, None, None, None, None, None,
+                           0, ctypes.byref(o), None, None, None, None, None, None, None, 0, None)
+    assert r == 0
+
+
+def test_binding_refuses_cpu_tensors():
+    import torch
+    with pytest.raises(TypeError):
+        negf.Device(torch.zeros((1, 2, 3, 3), dtype=torch.complex128), None)
