@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""Throughput of the batched recursive Green's function (RGF) hot path on GB300.
+
+Workload: a block-tridiagonal device of N = 70 slabs x 400 x 400 complex blocks (40 atoms x
+10 orbitals per slab, Si with 10% Ge as +0.2 eV on-site shifts), 512 energies in [-3, 3] eV x
+8 transverse k-points = 4096 (E, k) points, eta = 1e-6, synthetic seeded Hamiltonians.
+One step = one batch of points through the whole path: Sancho-Rubio lead self-energies,
+forward and backward sweeps, density / bond current / transmission, and the FP64 energy
+quadrature of the batch.  Inputs (8 k-point Hamiltonians, 2.9 GB) are resident in HBM; every
+step streams 358 MB of Hamiltonian blocks, more than the 129 MB L2.
+
+Prints one JSON line (metric energy-points/s).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORK = dict(N=70, b=400, n_E=512, n_k=8, ge_frac=0.1, eta=1e-6, seed=1001,
+            name="ballistic RGF, N=70 slabs x 400x400 blocks, alloy p(Ge)=0.1, 512 E x 8 k")
+METRIC = "RGF energy-points/s (leads + forward/backward sweeps + observables + FP64 quadrature)"
+PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--points-per-step", type=int, default=64)
+    ap.add_argument("--cpu-points", type=int, default=2)
+    ap.add_argument("--fp64-points", type=int, default=4)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the CPU-oracle, FP64-GPU and end-to-end side measurements")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+def build_hamiltonians():
+    from workloads import make_device, hamiltonian_k, k_grid, energy_grid_linspace
+    dev = make_device(WORK["N"], WORK["b"], WORK["seed"], ge_frac=WORK["ge_frac"], with_k=True)
+    ks, wk = k_grid(WORK["n_k"])
+    Hd = np.empty((WORK["n_k"], WORK["N"], WORK["b"], WORK["b"]), dtype=np.complex128)
+    for i, k in enumerate(ks):
+        Hd[i] = hamiltonian_k(dev, float(k))[0]
+    Hu = np.broadcast_to(dev.T, (WORK["n_k"],) + dev.T.shape)
+    E, wE = energy_grid_linspace(-3.0, 3.0, WORK["n_E"])
+    return dev, Hd, Hu, ks, wk, E, wE
+
+
+def point_index(n_pts_total, start, count):
+    idx = (np.arange(count) + start) % n_pts_total
+    return idx // WORK["n_E"], idx % WORK["n_E"]   # (k index, energy index)
+
+
+class Clocks:
+    """nvidia-smi sampling (read-only) while the timed region runs."""
+
+    def __init__(self, gpu_index):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[1]) for s in self.samples if len(s) > 2 and s[1].replace('.', '').isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) > 2 and s[2].replace('.', '').isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for n, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(self.samples),
+                "reasons": sorted(reasons)}
+
+
+def run_reference(args):
+    """CPU oracle on the host cores: each step solves one point of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    dev, Hd, Hu, ks, wk, E, wE = build_hamiltonians()
+    n_tot = WORK["n_E"] * WORK["n_k"]
+    for s in range(args.warmup):
+        kk, ee = point_index(n_tot, 1000 + s * 97, 1)
+        O.solve_point(Hd[kk[0]], dev.T, E[ee[0]], WORK["eta"], None)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        kk, ee = point_index(n_tot, s * 211, 1)
+        O.solve_point(Hd[kk[0]], dev.T, E[ee[0]], WORK["eta"], None)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    cores = _blas_threads()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": WORK["name"], "points_per_step": 1},
+        "cpu_baseline": {"value": v, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} points of the workload, one per step"},
+        "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import paper_1510_04686_gb300 as negf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    negf._build.build()
+    negf.library()
+    dvc = torch.device("cuda", torch.cuda.current_device())
+
+    dev_np, Hd, Hu, ks, wk, E, wE = build_hamiltonians()
+    Hd_t = torch.as_tensor(Hd, device=dvc)
+    Hu_t = torch.as_tensor(np.ascontiguousarray(Hu), device=dvc)
+    device = negf.Device(Hd_t, Hu_t)
+    prec = negf.PREC_MIXED if args.precision == "mixed" else negf.PREC_FP64
+    P = args.points_per_step
+    opt = negf.options(precision=prec, chunk=P)
+    n_tot = WORK["n_E"] * WORK["n_k"]
+    total_steps = args.warmup + args.steps
+    # per-step index tensors (rank-strided so ranks solve disjoint points)
+    step_E, step_sys, step_w = [], [], []
+    for s in range(total_steps):
+        kk, ee = point_index(n_tot, (s * world + rank) * P, P)
+        step_E.append(torch.as_tensor(E[ee], device=dvc))
+        step_sys.append(torch.as_tensor(kk.astype(np.int32), device=dvc))
+        step_w.append(torch.as_tensor(wE[ee] * wk[kk], device=dvc))
+    NB = WORK["N"] * WORK["b"]
+    n_int = torch.empty((total_steps, 1, NB), dtype=torch.float64, device=dvc)
+    j_int = torch.empty((total_steps, 1, WORK["N"] - 1), dtype=torch.float64, device=dvc)
+
+    def step(s):
+        lead = negf.lead_selfenergy(device, step_E[s], step_sys[s], opt)
+        out = negf.rgf_solve(device, step_E[s], step_sys[s], lead["sigma_R"], lead["sigma_L"], opt)
+        lib = negf.library()
+        st = torch.cuda.current_stream().cuda_stream
+        import ctypes
+        lib.negf_integrate(P, NB, 1, ctypes.c_void_p(step_w[s].data_ptr()), None,
+                           ctypes.c_void_p(out["density"].data_ptr()),
+                           ctypes.c_void_p(n_int[s].data_ptr()), ctypes.c_void_p(st))
+        lib.negf_integrate(P, WORK["N"] - 1, 1, ctypes.c_void_p(step_w[s].data_ptr()), None,
+                           ctypes.c_void_p(out["current"].data_ptr()),
+                           ctypes.c_void_p(j_int[s].data_ptr()), ctypes.c_void_p(st))
+        return out
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    negf.profile_reset()
+    negf.profile(True)
+    l0 = negf.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record()
+        for s in range(args.warmup, total_steps):
+            step(s)
+        ev1.record()
+        torch.cuda.synchronize()
+    launches = negf.launch_count() - l0
+    negf.profile(False)
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=dvc)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    n_launch, tc_ms, alg, hw = negf.profile_read(negf.PROF_TC_GEMM)
+    sl_n, sl_ms, _, _ = negf.profile_read(negf.PROF_SLICE)
+    points = args.steps * P * world
+    value = points / (ms / 1e3)
+
+    pk, pk_kind = peaks()
+    peak_bf16 = pk.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])
+    achieved = (alg / (tc_ms / 1e3)) / 1e12 if tc_ms > 0 else None
+    roofline = {
+        "kernel": "k_tc_gemm (tcgen05 split-BF16 complex GEMM)",
+        "bound": "tensor", "unit": "TFLOP/s",
+        "achieved": achieved, "peak": peak_bf16,
+        "frac": (achieved / peak_bf16) if achieved else None,
+        "peak_kind": f"bf16 dense sustained, {pk_kind}",
+        "algorithmic_flops_per_launch": alg / max(n_launch, 1),
+        "avg_launch_ms": tc_ms / max(n_launch, 1), "launches": n_launch,
+        "issued_bf16_tflops": (hw / (tc_ms / 1e3)) / 1e12 if tc_ms > 0 else None,
+        "issued_frac": ((hw / (tc_ms / 1e3)) / 1e12 / peak_bf16) if tc_ms > 0 else None,
+        "share_of_step": tc_ms / ms if ms > 0 else None,
+        "slicing_share_of_step": sl_ms / ms if ms > 0 else None,
+        "traffic": None,
+    }
+    line = {
+        "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16-slices->fp32 (fp64 storage)" if prec == negf.PREC_MIXED else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORK["name"], "points_per_step": P, "precision": args.precision,
+                   "l2": "inputs > L2: each step streams 358 MB of H blocks",
+                   "parallelism": f"replicas x{world}"},
+        "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roofline,
+    }
+    if rank == 0 and not args.no_extras:
+        line.update(extras(args, negf, torch, device, dvc, Hd, dev_np, E, wE, wk, prec))
+        if "fp64_gpu" in line:
+            line["speedup_vs_fp64_gpu"] = value / world / line["fp64_gpu"]["value"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def extras(args, negf, torch, device, dvc, Hd, dev_np, E, wE, wk, prec):
+    """Side measurements on rank 0: end-to-end with host buffers, FP64 GPU form, CPU oracle and
+    the accuracy of this run's points against the oracle."""
+    import oracle as O
+    out = {}
+    n_tot = WORK["n_E"] * WORK["n_k"]
+    P = args.points_per_step
+    NB = WORK["N"] * WORK["b"]
+    # ---- end to end: pinned host inputs -> device -> solve -> host results, per step
+    kk, ee = point_index(n_tot, 7 * P, P)
+    k0 = int(kk[0])
+    Hd_h = torch.as_tensor(Hd[k0][None]).pin_memory()
+    Hu_h = torch.as_tensor(dev_np.T[None]).pin_memory()
+    E_h = torch.as_tensor(E[ee]).pin_memory()
+    sys_h = torch.zeros(P, dtype=torch.int32).pin_memory()
+    dens_h = torch.empty((P, NB), dtype=torch.float64).pin_memory()
+    cur_h = torch.empty((P, WORK["N"] - 1), dtype=torch.float64).pin_memory()
+    tr_h = torch.empty((P,), dtype=torch.float64).pin_memory()
+    opt = negf.options(precision=prec, chunk=P)
+    e2e_steps = 2
+    h2d = Hd_h.numel() * 16 + Hu_h.numel() * 16 + P * 8 + P * 4
+    d2h = dens_h.numel() * 8 + cur_h.numel() * 8 + P * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hd = Hd_h.to(dvc, non_blocking=True)
+        hu = Hu_h.to(dvc, non_blocking=True)
+        Et = E_h.to(dvc, non_blocking=True)
+        st = sys_h.to(dvc, non_blocking=True)
+        d1 = negf.Device(hd, hu)
+        lead = negf.lead_selfenergy(d1, Et, st, opt)
+        r = negf.rgf_solve(d1, Et, st, lead["sigma_R"], lead["sigma_L"], opt)
+        dens_h.copy_(r["density"], non_blocking=True)
+        cur_h.copy_(r["current"], non_blocking=True)
+        tr_h.copy_(r["transmission"], non_blocking=True)
+        torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    out["e2e"] = {"value": e2e_steps * P / dt, "unit": "points/s", "h2d_bytes_per_step": int(h2d),
+                  "d2h_bytes_per_step": int(d2h), "steps": e2e_steps}
+    # ---- accuracy against the oracle and CPU baseline on a bounded sample
+    cp = max(1, args.cpu_points)
+    kk, ee = point_index(n_tot, 1234, cp)
+    Et = torch.as_tensor(E[ee], device=dvc)
+    st = torch.as_tensor(kk.astype(np.int32), device=dvc)
+    lead = negf.lead_selfenergy(device, Et, st, negf.options(precision=prec))
+    g = negf.rgf_solve(device, Et, st, lead["sigma_R"], lead["sigma_L"], negf.options(precision=prec))
+    g = {k: v.cpu().numpy() for k, v in g.items() if v is not None}
+    t0 = time.perf_counter()
+    refs = [O.solve_point(Hd[kk[i]], dev_np.T, E[ee[i]], WORK["eta"], None) for i in range(cp)]
+    dt = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": cp / dt, "unit": "points/s", "cores": _blas_threads(),
+                           "kind": "oracle",
+                           "sample": f"{cp} (E,k) points of the workload, numpy complex128"}
+
+    def rel(a, b):
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+    d_ref = np.array([r_["density"] for r_ in refs])
+    j_ref = np.array([r_["current"] for r_ in refs])
+    T_ref = np.array([r_["transmission"] for r_ in refs])
+    out["rel_err_vs_oracle"] = {
+        "density_per_point": rel(g["density"], d_ref),
+        "current_per_point": rel(g["current"], j_ref),
+        "transmission": float(np.abs(g["transmission"] - T_ref).max() / max(1.0, np.abs(T_ref).max())),
+        "points": cp, "norm": "inf-norm relative over the sample",
+    }
+    # ---- FP64 GPU form on a subset
+    if prec == negf.PREC_MIXED and args.fp64_points > 0:
+        fpn = args.fp64_points
+        kk, ee = point_index(n_tot, 99, fpn)
+        Et = torch.as_tensor(E[ee], device=dvc)
+        st = torch.as_tensor(kk.astype(np.int32), device=dvc)
+        o64 = negf.options(precision=negf.PREC_FP64, chunk=fpn)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        lead = negf.lead_selfenergy(device, Et, st, o64)
+        negf.rgf_solve(device, Et, st, lead["sigma_R"], lead["sigma_L"], o64)
+        ev1.record()
+        torch.cuda.synchronize()
+        v64 = fpn / (ev0.elapsed_time(ev1) / 1e3)
+        out["fp64_gpu"] = {"value": v64, "unit": "points/s", "points": fpn,
+                           "sample": f"{fpn} points of the workload in one batch"}
+    return out
+
+
+if __name__ == "__main__":
+    main()

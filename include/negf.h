@@ -202,6 +202,46 @@ negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, const double
 negf_status negf_integrate(int32_t n_pts, int32_t len, int32_t n_groups, const double* w,
                            const int32_t* group, const double* in, double* out, void* stream);
 
+/* ---- block operations the sweeps are built from ------------------------------------------
+ * Batched complex GEMM  C[p] = alpha op(A[p]) op(B[p]) + beta C[p]  (Eqs. 1-2 are evaluated
+ * block by block as such products).  complex128 row-major; op 0 = none, 1 = transpose,
+ * 2 = conjugate transpose; op(A) is M x K, op(B) is K x N; strides are in complex elements
+ * between batch items (0 = the same matrix for every item; C needs a nonzero stride when
+ * n_batch > 1).  FP64 form: CUDA cores.  Mixed form: tensor cores with exact split-BF16
+ * slices (error ~2^-45 relative to max|A| max|B| per row and column).  n_batch <= 65535. */
+size_t negf_zgemm_workspace_size(int32_t precision, int32_t n_batch, int32_t M, int32_t N,
+                                 int32_t K);
+negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, int32_t N,
+                               int32_t K, double alpha_re, double alpha_im, const double* A,
+                               int64_t strideA, int32_t lda, int32_t opA, const double* B,
+                               int64_t strideB, int32_t ldb, int32_t opB, double beta_re,
+                               double beta_im, double* C, int64_t strideC, int32_t ldc,
+                               void* ws, size_t ws_bytes, void* stream);
+
+/* Batched block inverse X[p] = M[p]^-1 (the (z - H - Sigma)^-1 of Eq. 1), n x n complex128,
+ * contiguous items.  Gauss-Jordan with partial pivoting (FP64 pivot search and reciprocal).
+ * FP64 form: FP64 elimination, M is destroyed.  Mixed form: FP32 elimination followed by
+ * `refine_steps` Newton-Schulz steps X <- X + X (I - M X) with tensor-core products; M is
+ * kept.  status[p] gets NEGF_PT_SINGULAR on an exactly zero pivot. */
+size_t negf_zinv_workspace_size(int32_t precision, int32_t n_batch, int32_t n);
+negf_status negf_zinv_batched(int32_t precision, int32_t n_batch, int32_t n, double* M,
+                              double* X, int32_t refine_steps, int32_t* status, void* ws,
+                              size_t ws_bytes, void* stream);
+
+/* ---- accounting ----------------------------------------------------------------------------
+ * Instrumentation for benchmarks, not part of the method.  negf_launch_count() is the number
+ * of kernels this library has launched since it was loaded.  With profiling on, every launch of
+ * the tensor-core GEMM kernel (kind 0) and of its operand slicing (kind 1) is bracketed by CUDA
+ * events on its own stream; negf_profile_read synchronises those events and returns the
+ * cumulative launches and milliseconds of the kind since the last negf_profile_reset. */
+void negf_profile_enable(int32_t on);
+void negf_profile_reset(void);
+negf_status negf_profile_read(int32_t kind, long long* launches, double* total_ms);
+/* Flops dispatched to kind 0 since the last reset: complex algorithmic 8 M N K per batch item,
+ * and the BF16 tensor-core flops actually issued (all slice products over the padded tiles). */
+negf_status negf_profile_flops(int32_t kind, double* algorithmic, double* hardware);
+long long negf_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -12,6 +12,14 @@ from .negf import (  # noqa: F401
     scba_step,
     rgf_adjoint,
     integrate,
+    zgemm,
+    zinv,
+    profile,
+    profile_reset,
+    profile_read,
+    launch_count,
+    PROF_TC_GEMM,
+    PROF_SLICE,
     workspace_size,
     library,
     PREC_FP64,

@@ -1,0 +1,95 @@
+// Block-level entry points: the batched complex GEMM and block inverse that the sweeps are
+// built from, exposed for callers that assemble their own recursions.
+#include "engine.cuh"
+#include "tc_gemm.cuh"
+
+using namespace negf;
+
+namespace {
+bool prec_ok(int p) { return p == NEGF_PREC_FP64 || p == NEGF_PREC_MIXED; }
+}  // namespace
+
+extern "C" {
+
+size_t negf_zgemm_workspace_size(int32_t precision, int32_t n_batch, int32_t M, int32_t N,
+                                 int32_t K) {
+  if (!prec_ok(precision) || n_batch < 1 || M < 1 || N < 1 || K < 1) return 0;
+  if (precision == NEGF_PREC_FP64) return 256;
+  return tc_ws_bytes(n_batch, M, N, K) + 1024;
+}
+
+negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, int32_t N,
+                               int32_t K, double alpha_re, double alpha_im, const double* A,
+                               int64_t strideA, int32_t lda, int32_t opA, const double* B,
+                               int64_t strideB, int32_t ldb, int32_t opB, double beta_re,
+                               double beta_im, double* C, int64_t strideC, int32_t ldc,
+                               void* ws, size_t ws_bytes, void* stream) {
+  if (!prec_ok(precision) || n_batch < 0 || M < 0 || N < 0 || K < 0) return NEGF_ERR_ARG;
+  if (n_batch == 0 || M == 0 || N == 0) return NEGF_OK;
+  if (!A || !B || !C || opA < 0 || opA > 2 || opB < 0 || opB > 2) return NEGF_ERR_ARG;
+  if (n_batch > 65535) return NEGF_ERR_UNSUPPORTED;
+  const int rowsA = opA == OP_N ? M : K, colsA = opA == OP_N ? K : M;
+  const int rowsB = opB == OP_N ? K : N, colsB = opB == OP_N ? N : K;
+  (void)rowsA;
+  (void)rowsB;
+  if (lda < colsA || ldb < colsB || ldc < N) return NEGF_ERR_ARG;
+  if (strideC == 0 && n_batch > 1) return NEGF_ERR_ARG;
+  if (ws_bytes < negf_zgemm_workspace_size(precision, n_batch, M, N, K) || !ws)
+    return NEGF_ERR_NOMEM;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  BMc<double> a{reinterpret_cast<const z64*>(A), strideA, nullptr, lda};
+  BMc<double> b{reinterpret_cast<const z64*>(B), strideB, nullptr, ldb};
+  BM<double> c{reinterpret_cast<z64*>(C), strideC, nullptr, ldc};
+  BMc<double> none{nullptr, 0, nullptr, 0};
+  const z64 al = mkc(alpha_re, alpha_im), be = mkc(beta_re, beta_im), zero = mkc(0.0, 0.0);
+  cudaError_t e;
+  if (precision == NEGF_PREC_FP64) {
+    if (K == 0) return NEGF_ERR_UNSUPPORTED;
+    e = gemm_simt<double>(s, n_batch, M, N, K, al, a, opA, b, opB, be, c, zero, none, nullptr);
+  } else {
+    if (K == 0) return NEGF_ERR_UNSUPPORTED;
+    size_t off = 0;
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
+    TcWs tw;
+    tc_ws_carve(base, off, n_batch, M, N, K, tw);
+    e = tc_gemm(s, n_batch, M, N, K, al, a, opA, b, opB, be, c, zero, none, false, nullptr, tw);
+  }
+  return e == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
+}
+
+size_t negf_zinv_workspace_size(int32_t precision, int32_t n_batch, int32_t n) {
+  if (!prec_ok(precision) || n_batch < 1 || n < 1) return 0;
+  size_t off = 0;
+  EngineWs w;
+  carve_engine(nullptr, off, n_batch, n, precision, w);
+  return off + 1024;
+}
+
+negf_status negf_zinv_batched(int32_t precision, int32_t n_batch, int32_t n, double* M,
+                              double* X, int32_t refine_steps, int32_t* status, void* ws,
+                              size_t ws_bytes, void* stream) {
+  if (!prec_ok(precision) || n_batch < 0 || n < 0 || refine_steps < 0 || refine_steps > 8)
+    return NEGF_ERR_ARG;
+  if (n_batch == 0 || n == 0) return NEGF_OK;
+  if (!M || !X || !status) return NEGF_ERR_ARG;
+  if (n_batch > 65535) return NEGF_ERR_UNSUPPORTED;
+  if (!ws || ws_bytes < negf_zinv_workspace_size(precision, n_batch, n)) return NEGF_ERR_NOMEM;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(status, 0, (size_t)n_batch * sizeof(int32_t), s) != cudaSuccess)
+    return NEGF_ERR_CUDA;
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 255) & ~uintptr_t(255));
+  size_t off = 0;
+  EngineWs w;
+  carve_engine(base, off, n_batch, n, precision, w);
+  negf_options o;
+  negf_default_options(&o);
+  o.precision = precision;
+  o.refine_steps = refine_steps;
+  Engine eng(s, &o, w, n);
+  const long long nn = (long long)n * n;
+  cudaError_t e = eng.inv(n_batch, BM<double>{reinterpret_cast<z64*>(M), nn, nullptr, n},
+                          BM<double>{reinterpret_cast<z64*>(X), nn, nullptr, n}, status, nullptr);
+  return e == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -3,6 +3,8 @@
 // Gauss-Jordan.  Mixed form: tensor-core GEMM of exact split-BF16 slices and an FP32
 // Gauss-Jordan inverse polished by Newton-Schulz steps X <- X + X (I - M X).
 #pragma once
+#include <utility>
+
 #include "common.cuh"
 
 namespace negf {

@@ -2,6 +2,7 @@
 // the recursive Green's function sweeps (Eqs. 1-2 evaluated block by block): every product
 // of two b x b blocks of G, g, H or Sigma goes through here when precision == FP64.
 #include "common.cuh"
+#include "profile.cuh"
 
 namespace negf {
 
@@ -114,6 +115,7 @@ cudaError_t gemm_simt(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc
   if (P <= 0 || M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((N + BNT - 1) / BNT, (M + BMT - 1) / BMT, P);
   k_gemm_simt<R><<<grid, 256, 0, s>>>(M, N, K, alpha, A, opA, B, opB, beta, C, gamma, D, active);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "profile.cuh"
 
 namespace negf {
 
@@ -270,6 +271,7 @@ cudaError_t gj_inverse(cudaStream_t s, int P, int n, BM<R> M, BM<R> X, cx<R>* U,
                                          (int)kSmemBudget + 1024);
     if (e != cudaSuccess) return e;
     k_gj_small<R><<<P, kThreads, smem, s>>>(n, M, X, status, active);
+    count_launch();
     return cudaGetLastError();
   }
   const int nb = gj_panel_width(n, eb);
@@ -280,6 +282,7 @@ cudaError_t gj_inverse(cudaStream_t s, int P, int n, BM<R> M, BM<R> X, cx<R>* U,
     const int w = std::min(nb, n - k0);
     size_t smem = (size_t)n * w * eb + (size_t)n * eb;
     k_gj_panel<R><<<P, kThreads, smem, s>>>(n, k0, w, nb, M, U, T, piv, status, active);
+    count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     BMc<R> Ua{U, (long long)n * nb, nullptr, nb};
     BMc<R> Ta{T, (long long)nb * n, nullptr, n};
@@ -289,6 +292,7 @@ cudaError_t gj_inverse(cudaStream_t s, int P, int n, BM<R> M, BM<R> X, cx<R>* U,
     if (e != cudaSuccess) return e;
   }
   k_gj_unpermute<R><<<P, kThreads, n * sizeof(int), s>>>(n, M, X, piv, active);
+  count_launch();
   return cudaGetLastError();
 }
 

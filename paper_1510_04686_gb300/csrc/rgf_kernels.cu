@@ -1,6 +1,7 @@
 // Elementwise and reduction kernels of the RGF sweeps: assembly of z - H - V - Sigma, source
 // terms of Eq. (2), anti-Hermitian projection, observables of Eqs. (7)-(8) and transmission,
 // and the per-step pieces of the Sancho-Rubio decimation.  All on complex128 storage.
+#include "profile.cuh"
 #include "rgf_kernels.cuh"
 
 namespace negf {
@@ -350,6 +351,7 @@ cudaError_t launch_assemble(cudaStream_t s, int P, int b, const double* E, doubl
                             const int32_t* active) {
   k_assemble<<<grid2((long long)b * b, P), kT, 0, s>>>(b, E, eta, Hd, V, scat, scat_stride,
                                                        e_idx, Y, SigA, SigB, M, active);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_source(cudaStream_t s, int P, int b, const z64* scat, long long scat_stride,
@@ -357,61 +359,72 @@ cudaError_t launch_source(cudaStream_t s, int P, int b, const z64* scat, long lo
                           BM<double> S, const int32_t* active) {
   k_source<<<grid2((long long)b * b, P), kT, 0, s>>>(b, scat, scat_stride, e_idx, SigA, SigB, S,
                                                      active);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_antiherm(cudaStream_t s, int P, int b, BMc<double> S, BM<double> O,
                             const int32_t* active) {
   k_antiherm<<<grid2((long long)b * b, P), kT, 0, s>>>(b, S, O, active);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_slab_obs(cudaStream_t s, int P, int b, int i, int nb_tot, BMc<double> G,
                             BMc<double> GL, double* density, z64* dGR, z64* dGL,
                             const int32_t* active) {
   k_slab_obs<<<grid2(b, P), kT, 0, s>>>(b, i, nb_tot, G, GL, density, dGR, dGL, active);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_bond_current(cudaStream_t s, int P, int b, BMc<double> Tm, BMc<double> U,
                                 BMc<double> Q, double* out, long long out_stride,
                                 const int32_t* active) {
   k_bond_current<<<P, kT, 0, s>>>(b, Tm, U, Q, out, out_stride, active);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_gamma(cudaStream_t s, int P, int b, BMc<double> Sig, BM<double> Gam,
                          const int32_t* active) {
   k_gamma<<<grid2((long long)b * b, P), kT, 0, s>>>(b, Sig, Gam, active);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_transmission(cudaStream_t s, int P, int b, BMc<double> Gam, BMc<double> G,
                                 BMc<double> Y, BMc<double> Z, double* out,
                                 const int32_t* active) {
   k_transmission<<<P, kT, 0, s>>>(b, Gam, G, Y, Z, out, active);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_sr_init(cudaStream_t s, int P2, int b, int N, BMc<double> Hd, BMc<double> Hu,
                            BM<double> eps_s, BM<double> eps, BM<double> al, BM<double> be,
                            double* scale) {
   k_sr_init<<<dim3(1, P2), kT, 0, s>>>(b, N, Hd, Hu, eps_s, eps, al, be, scale);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_zminus(cudaStream_t s, int P2, int b, const double* E, double eta,
                           BMc<double> X, BM<double> M, const int32_t* active) {
   k_zminus<<<grid2((long long)b * b, P2), kT, 0, s>>>(b, E, eta, X, M, active);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_add2(cudaStream_t s, int P2, int b, BMc<double> T1, BM<double> A1,
                         BM<double> A2, const int32_t* active) {
   k_add2<<<grid2((long long)b * b, P2), kT, 0, s>>>(b, T1, A1, A2, active);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_sr_check(cudaStream_t s, int P2, int b, int it, double tol, BMc<double> al,
                             BMc<double> be, const double* scale, int32_t* active,
                             int32_t* iters, int32_t* n_active) {
   k_sr_check<<<P2, kT, 0, s>>>(b, it, tol, al, be, scale, active, iters, n_active);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_lead_lesser(cudaStream_t s, int P2, int b, const double* E, double mu_L,
                                double mu_R, double kT_, BMc<double> Gam, BM<double> Les) {
   k_lead_lesser<<<grid2((long long)b * b, P2), kT, 0, s>>>(b, E, mu_L, mu_R, kT_, Gam, Les);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_sr_status(cudaStream_t s, int P, const int32_t* active,
@@ -419,17 +432,20 @@ cudaError_t launch_sr_status(cudaStream_t s, int P, const int32_t* active,
                              int max_iter, int32_t* status) {
   k_sr_status<<<(P + kT - 1) / kT, kT, 0, s>>>(P, active, item_status, iters_in, iters_out,
                                                max_iter, status);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_check_finite(cudaStream_t s, const double* x, long long per_pt, int P,
                                 int32_t* status) {
   if (per_pt <= 0 || P <= 0) return cudaSuccess;
   k_check_finite<<<grid2(per_pt, P), kT, 0, s>>>(x, per_pt, P, status);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_clamp_index(cudaStream_t s, int P, const int32_t* in, int n, int32_t* out,
                                int32_t* status) {
   k_clamp_index<<<(P + kT - 1) / kT, kT, 0, s>>>(P, in, n, out, status);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_fill_i32(cudaStream_t s, int32_t* a, long long n, int32_t v) {
@@ -437,12 +453,14 @@ cudaError_t launch_fill_i32(cudaStream_t s, int32_t* a, long long n, int32_t v) 
   long long bx = (n + kT - 1) / kT;
   if (bx > 1024) bx = 1024;
   k_fill_i32<<<(unsigned)bx, kT, 0, s>>>(a, n, v);
+  count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_integrate(cudaStream_t s, int P, int len, int n_groups, const double* w,
                              const int32_t* group, const double* in, double* out) {
   for (int g = 0; g < n_groups; ++g) {
     k_integrate<<<(len + kT - 1) / kT, kT, 0, s>>>(P, len, w, group, g, in, out);
+    count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

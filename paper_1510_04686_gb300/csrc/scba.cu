@@ -1,6 +1,7 @@
 // Self-consistent Born step of the phonon self-energies, Eqs. (4)-(6), on orbital-diagonal
 // arrays.  Bandwidth-bound gather over k' and the energy shift E +- hbar omega.
 #include "common.cuh"
+#include "profile.cuh"
 
 namespace negf {
 namespace {
@@ -78,5 +79,6 @@ extern "C" negf_status negf_scba_step(int32_t n_k, int32_t n_E, int32_t n_orb, c
                                           reinterpret_cast<z64*>(sigma_R),
                                           reinterpret_cast<z64*>(sigma_L),
                                           reinterpret_cast<unsigned long long*>(delta_out));
+  count_launch();
   return cudaGetLastError() == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
 }

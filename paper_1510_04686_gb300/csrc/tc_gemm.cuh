@@ -1,0 +1,38 @@
+// Tensor-core complex GEMM with FP64-class accuracy from exact split-BF16 products.
+//
+//   C = alpha op(A) op(B) + beta C + gamma D (+ I)       (complex128 in and out)
+//
+// Each operand row (A) / column (B) is scaled by a power of two and cut into S fixed-point
+// slices of beta bits stored as BF16 (exact).  Slice products are exact in BF16 x BF16 -> FP32
+// and, with beta chosen from K, every group of slice pairs of one order s + t - 1 sums to an
+// integer below 2^24 and is exact in its FP32 TMEM accumulator (the tensor core's accumulation
+// truncates, so inexact groups would lose bits linearly in K); the groups are added in FP64 in
+// the epilogue.  Products of order > S are dropped (below 2^-48 of the scale).  The complex product
+// uses the real embedding  [Re A, Im A] x [[Re B, Im B], [-Im B, Re B]]  so that one MMA chain
+// produces interleaved (re, im) outputs.
+#pragma once
+#include "common.cuh"
+
+namespace negf {
+
+struct TcWs {
+  void* slicesA;        // bf16 [P][S][M][L]
+  void* slicesB;        // bf16 [P][S][2N][L]
+  int32_t* expA;        // [P][M]
+  int32_t* expB;        // [P][N]
+  double* T64;          // [P][M][2N] partial sums between accumulator groups
+  int32_t* err;         // device error word (bounded waits that gave up)
+};
+
+// Bytes of TcWs scratch for P items of an M x N x K product.
+size_t tc_ws_bytes(int P, int M, int N, int K);
+void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, TcWs& w);
+
+// Slices and exactness parameters used for a contraction length K (complex).
+void tc_plan(int K, int* beta, int* S);
+
+cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<double> A,
+                    int opA, BMc<double> B, int opB, z64 beta, BM<double> C, z64 gamma,
+                    BMc<double> D, bool add_identity, const int32_t* active, const TcWs& ws);
+
+}  // namespace negf

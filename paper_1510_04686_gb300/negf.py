@@ -46,7 +46,10 @@ class _Opt(ctypes.Structure):
 _LIB = None
 EXPORTS = ("negf_default_options", "negf_abi_version", "negf_status_string",
            "negf_workspace_size", "negf_lead_selfenergy", "negf_rgf_solve", "negf_scba_step",
-           "negf_rgf_adjoint", "negf_integrate")
+           "negf_rgf_adjoint", "negf_integrate", "negf_zgemm_workspace_size",
+           "negf_zgemm_batched", "negf_zinv_workspace_size", "negf_zinv_batched",
+           "negf_profile_enable", "negf_profile_reset", "negf_profile_read", "negf_profile_flops",
+           "negf_launch_count")
 
 
 def library():
@@ -81,6 +84,29 @@ def library():
     lib.negf_rgf_adjoint.restype = c_int32
     lib.negf_integrate.argtypes = [c_int32, c_int32, c_int32, P, P, P, P, P]
     lib.negf_integrate.restype = c_int32
+    lib.negf_zgemm_workspace_size.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32]
+    lib.negf_zgemm_workspace_size.restype = c_size_t
+    i64 = ctypes.c_int64
+    lib.negf_zgemm_batched.argtypes = [c_int32, c_int32, c_int32, c_int32, c_int32, c_double,
+                                       c_double, P, i64, c_int32, c_int32, P, i64, c_int32,
+                                       c_int32, c_double, c_double, P, i64, c_int32, P, c_size_t,
+                                       P]
+    lib.negf_zgemm_batched.restype = c_int32
+    lib.negf_zinv_workspace_size.argtypes = [c_int32, c_int32, c_int32]
+    lib.negf_zinv_workspace_size.restype = c_size_t
+    lib.negf_zinv_batched.argtypes = [c_int32, c_int32, c_int32, P, P, c_int32, P, P, c_size_t,
+                                      P]
+    lib.negf_zinv_batched.restype = c_int32
+    lib.negf_profile_enable.argtypes = [c_int32]
+    lib.negf_profile_enable.restype = None
+    lib.negf_profile_reset.argtypes = []
+    lib.negf_profile_reset.restype = None
+    lib.negf_profile_read.argtypes = [c_int32, POINTER(ctypes.c_longlong), POINTER(c_double)]
+    lib.negf_profile_read.restype = c_int32
+    lib.negf_profile_flops.argtypes = [c_int32, POINTER(c_double), POINTER(c_double)]
+    lib.negf_profile_flops.restype = c_int32
+    lib.negf_launch_count.argtypes = []
+    lib.negf_launch_count.restype = ctypes.c_longlong
     _LIB = lib
     return lib
 
@@ -270,3 +296,78 @@ def integrate(values, w, group=None, n_groups=1):
     _check(library().negf_integrate(n, ln, n_groups, _ptr(w), _ptr(group), _ptr(values),
                                     _ptr(out), _stream()), "negf_integrate")
     return out
+
+
+_OPS = {"N": 0, "T": 1, "C": 2}
+
+
+def zgemm(A, B, C=None, alpha=1.0, beta=0.0, opA="N", opB="N", precision=PREC_FP64):
+    """Batched C = alpha op(A) op(B) + beta C on [n, rows, cols] complex128 CUDA tensors.
+
+    A or B may be 2-D (shared by every batch item)."""
+    def bview(X, name):
+        _need(X, torch.complex128, name)
+        if X.dim() == 2:
+            return X, 0
+        return X, X.shape[1] * X.shape[2]
+    A, sA = bview(A, "A")
+    B, sB = bview(B, "B")
+    nb = max(A.shape[0] if A.dim() == 3 else 1, B.shape[0] if B.dim() == 3 else 1)
+    ra, ca = A.shape[-2], A.shape[-1]
+    rb, cb = B.shape[-2], B.shape[-1]
+    M, K = (ra, ca) if opA == "N" else (ca, ra)
+    K2, N = (rb, cb) if opB == "N" else (cb, rb)
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.zeros((nb, M, N), dtype=torch.complex128, device=A.device)
+    _need(C, torch.complex128, "C", (nb, M, N))
+    ws_n = int(library().negf_zgemm_workspace_size(precision, nb, M, N, K))
+    ws = _workspace(ws_n, A.device)
+    a = complex(alpha)
+    b = complex(beta)
+    _check(library().negf_zgemm_batched(precision, nb, M, N, K, a.real, a.imag, _ptr(A), sA,
+                                        A.shape[-1], _OPS[opA], _ptr(B), sB, B.shape[-1],
+                                        _OPS[opB], b.real, b.imag, _ptr(C), M * N, N, _ptr(ws),
+                                        ws_n, _stream()), "negf_zgemm_batched")
+    return C
+
+
+def zinv(M, precision=PREC_FP64, refine_steps=2):
+    """Batched inverse of [n, b, b] complex128; returns (X, status).  M is consumed in FP64."""
+    _need(M, torch.complex128, "M")
+    nb, n, _ = M.shape
+    X = torch.empty_like(M)
+    st = torch.empty((nb,), dtype=torch.int32, device=M.device)
+    ws_n = int(library().negf_zinv_workspace_size(precision, nb, n))
+    ws = _workspace(ws_n, M.device)
+    _check(library().negf_zinv_batched(precision, nb, n, _ptr(M), _ptr(X), refine_steps,
+                                       _ptr(st), _ptr(ws), ws_n, _stream()),
+           "negf_zinv_batched")
+    return X, st
+
+
+PROF_TC_GEMM, PROF_SLICE = 0, 1
+
+
+def profile(enable: bool):
+    library().negf_profile_enable(1 if enable else 0)
+
+
+def profile_reset():
+    library().negf_profile_reset()
+
+
+def profile_read(kind=PROF_TC_GEMM):
+    """(launches, total_ms, algorithmic_flops, issued_bf16_flops) of a kernel kind."""
+    n = ctypes.c_longlong(0)
+    ms = c_double(0.0)
+    _check(library().negf_profile_read(kind, ctypes.byref(n), ctypes.byref(ms)), "profile_read")
+    a = c_double(0.0)
+    h = c_double(0.0)
+    _check(library().negf_profile_flops(kind, ctypes.byref(a), ctypes.byref(h)), "profile_flops")
+    return int(n.value), float(ms.value), float(a.value), float(h.value)
+
+
+def launch_count() -> int:
+    return int(library().negf_launch_count())
