@@ -228,6 +228,24 @@ negf_status negf_zinv_batched(int32_t precision, int32_t n_batch, int32_t n, dou
                               double* X, int32_t refine_steps, int32_t* status, void* ws,
                               size_t ws_bytes, void* stream);
 
+/* Allocation-free variant of negf_zinv_batched, FP64 form only (the paper has no counterpart;
+ * this exists for callers that cannot allocate device memory at the point of the call, e.g. a
+ * host application whose device memory is owned by an arena reserved at start-up, or code that
+ * must not call cudaMalloc after initialisation because it can synchronise the device and fail
+ * once memory is fragmented).  Same inputs and outputs as negf_zinv_batched with
+ * precision = NEGF_PREC_FP64 and no workspace: the elimination scratch lives in a fixed 32 MiB
+ * device array inside this library, reserved on every GPU that loads it until the process
+ * exits.  The scratch needed, about n_batch * n * (2 * 16 * nb + 4) bytes with the panel width
+ * nb <= 32 (none at all for n up to about 100, which is done in shared memory), must fit those
+ * 32 MiB, else the call returns NEGF_ERR_NOMEM before launching anything.  The first call on a
+ * device looks up the array's device address for that device, with the device current, and
+ * keeps it.  Every call on a device shares the one array, which keeps the last call's
+ * contents: calls that overlap on the GPU (different streams, or different host threads)
+ * race on it and must be serialised by the caller.  It calls no cudaMalloc or cudaFree.
+ * M is destroyed; status[p] gets NEGF_PT_SINGULAR on an exactly zero pivot. */
+negf_status negf_zinv_batched_noalloc(int32_t n_batch, int32_t n, double* M, double* X,
+                                      int32_t* status, void* stream);
+
 /* ---- accounting ----------------------------------------------------------------------------
  * Instrumentation for benchmarks, not part of the method.  negf_launch_count() is the number
  * of kernels this library has launched since it was loaded.  With profiling on, every launch of

@@ -49,7 +49,7 @@ EXPORTS = ("negf_default_options", "negf_abi_version", "negf_status_string",
            "negf_rgf_adjoint", "negf_integrate", "negf_zgemm_workspace_size",
            "negf_zgemm_batched", "negf_zinv_workspace_size", "negf_zinv_batched",
            "negf_profile_enable", "negf_profile_reset", "negf_profile_read", "negf_profile_flops",
-           "negf_launch_count")
+           "negf_launch_count", "negf_zinv_batched_noalloc")
 
 
 def library():
@@ -107,6 +107,8 @@ def library():
     lib.negf_profile_flops.restype = c_int32
     lib.negf_launch_count.argtypes = []
     lib.negf_launch_count.restype = ctypes.c_longlong
+    lib.negf_zinv_batched_noalloc.argtypes = [c_int32, c_int32, P, P, P, P]
+    lib.negf_zinv_batched_noalloc.restype = c_int32
     _LIB = lib
     return lib
 
