@@ -19,6 +19,8 @@ from .negf import (  # noqa: F401
     profile_read,
     launch_count,
     PROF_TC_GEMM,
+    RGFFunction,
+    rgf,
     PROF_SLICE,
     workspace_size,
     library,

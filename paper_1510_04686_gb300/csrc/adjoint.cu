@@ -1,22 +1,413 @@
-// Reverse-mode derivative of the RGF observables with respect to the on-site potential.
+// Reverse-mode derivative of the RGF observables with respect to the on-site potential V (the
+// e Phi of Eq. 1).  For L = sum_p [sum_j c_pj n_j(p) + sum_i d_pi j_i(p)] with n_j = Im G^<_jj/2pi
+// and j_i = 2 Re Tr[t_i G^<_{i+1,i}], the sweep of negf_rgf_solve is run once more keeping its
+// forward values, then every block operation is reversed:
+//   Y = A B        ->  Abar += Ybar B^H,  Bbar += A^H Ybar
+//   Y = M^-1       ->  Mbar  = -Y^H Ybar Y^H
+//   G^< = AH(S)    ->  Sbar  = AH(G^<bar),   AH(X) = (X - X^H) / 2
+//   M = ... - diag(V)  ->  Vbar_q = -Re Mbar_qq
+// with xbar = dL/dRe x + i dL/dIm x.  The backward sweep is reversed first (slab 0 upwards),
+// then the forward sweep (slab N-1 downwards).  Lead and scattering self-energies are held fixed.
+#include <algorithm>
+#include <vector>
+
 #include "engine.cuh"
+#include "profile.cuh"
+#include "rgf_kernels.cuh"
 
 namespace negf {
+namespace {
+
+constexpr int kT = 256;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+inline dim3 g2(long long work, int P) {
+  long long bx = (work + kT - 1) / kT;
+  bx = std::max(1LL, std::min(bx, 64LL));
+  return dim3((unsigned)bx, (unsigned)P);
+}
+
+// X[p] = 0 except the diagonal i c_pj / (2 pi) (seed of the density cotangent)
+__global__ void k_seed_density(int b, int i, int NB, const double* c, BM<double> X) {
+  const int p = blockIdx.y;
+  z64* x = bat(X, p);
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (long long)b * b;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(k / b), col = (int)(k % b);
+    double v = 0.0;
+    if (c && r == col) v = c[(long long)p * NB + (long long)i * b + r] / kTwoPi;
+    x[(long long)r * X.ld + col] = mkc(0.0, v);
+  }
+}
+
+// X[p] = d_p t^H (cotangent of Re Tr[t X] scaled by d_p); d NULL gives zero
+__global__ void k_set_dtH(int b, BMc<double> Tm, const double* d, long long d_stride, BM<double> X) {
+  const int p = blockIdx.y;
+  const z64* t = bat(Tm, p);
+  z64* x = bat(X, p);
+  const double dp = d ? d[(long long)p * d_stride] : 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (long long)b * b;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(k / b), col = (int)(k % b);
+    z64 v = t[(long long)col * Tm.ld + r];
+    x[(long long)r * X.ld + col] = mkc(dp * v.re, -dp * v.im);
+  }
+}
+
+// Y += X
+__global__ void k_axpy(long long n, const z64* x, z64* y) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    y[k] = y[k] + x[k];
+}
+
+// vb[p][i b + q] = -Re Mbar_qq
+__global__ void k_vbar(int b, int i, int NB, BMc<double> Mb, double* vb) {
+  const int p = blockIdx.y;
+  const z64* m = bat(Mb, p);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < b; q += gridDim.x * blockDim.x)
+    vb[(long long)p * NB + (long long)i * b + q] = -m[(long long)q * Mb.ld + q].re;
+}
+
+// out[j] (+)= sum over p in order of vb[p][j]
+__global__ void k_sum_points(int P, int NB, const double* vb, double* out, int accumulate) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= NB) return;
+  double acc = accumulate ? out[j] : 0.0;
+  for (int p = 0; p < P; ++p) acc += vb[(long long)p * NB + j];
+  out[j] = acc;
+}
+
+template <class T>
+T* take(char* base, size_t& off, size_t n) {
+  size_t a = (off + 255) & ~size_t(255);
+  off = a + n * sizeof(T);
+  return base ? reinterpret_cast<T*>(base + a) : nullptr;
+}
+
+struct AdjWs {
+  int32_t *sys, *erow;
+  z64 *gF, *glF, *Gb, *GLb, *Lb, *gbar, *glbar, *Lbar;
+  z64 *Gc, *Gn, *GLc, *GLn;                      // rolling cotangents of G, G^<
+  z64 *t[14];                                    // temporaries
+  double* vb;                                    // per-point V cotangent
+  EngineWs eng;
+};
+
+void carve_adj(char* base, size_t& off, int P, int b, int N, int prec, AdjWs& w) {
+  const size_t PB = (size_t)P * b * b;
+  const size_t N1 = (size_t)std::max(N - 1, 1);
+  w.sys = take<int32_t>(base, off, P);
+  w.erow = take<int32_t>(base, off, P);
+  w.gF = take<z64>(base, off, N * PB);
+  w.glF = take<z64>(base, off, N * PB);
+  w.Gb = take<z64>(base, off, N * PB);
+  w.GLb = take<z64>(base, off, N * PB);
+  w.Lb = take<z64>(base, off, N1 * PB);
+  w.gbar = take<z64>(base, off, N * PB);
+  w.glbar = take<z64>(base, off, N * PB);
+  w.Lbar = take<z64>(base, off, N1 * PB);
+  w.Gc = take<z64>(base, off, PB);
+  w.Gn = take<z64>(base, off, PB);
+  w.GLc = take<z64>(base, off, PB);
+  w.GLn = take<z64>(base, off, PB);
+  for (int k = 0; k < 14; ++k) w.t[k] = take<z64>(base, off, PB);
+  w.vb = take<double>(base, off, (size_t)P * N * b);
+  carve_engine(base, off, P, b, prec, w.eng);
+}
+
+#define CK(x)                                    \
+  do {                                           \
+    cudaError_t e_ = (x);                        \
+    if (e_ != cudaSuccess) return NEGF_ERR_CUDA; \
+  } while (0)
+
+struct AdjArgs {
+  const negf_device* dev;
+  const double* E;
+  const int32_t* sys;
+  const double* V;
+  const z64* sigR;
+  const z64* sigL;
+  const z64* scatR;
+  const z64* scatL;
+  const int32_t* e_idx;
+  int32_t n_rows;
+  const negf_options* opt;
+  const double* nbar;   // [P][N b] or NULL
+  const double* jbar;   // [P][N-1] or NULL
+  double* Vbar;         // [N b]
+  bool accumulate;
+  int32_t* status;
+};
+
+negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_t s) {
+  const negf_device* dev = a.dev;
+  const int b = dev->block, N = dev->n_slabs;
+  const size_t bb = (size_t)b * b, PB = (size_t)P * bb;
+  const int NB = N * b;
+  const z64 one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0), two = mkc(2.0, 0.0), mone = mkc(-1.0, 0.0);
+  const BMc<double> none{nullptr, 0, nullptr, 0};
+  size_t off = 0;
+  AdjWs w;
+  carve_adj(wsbase, off, P, b, N, a.opt->precision, w);
+  Engine eng(s, a.opt, w.eng, b);
+  CK(launch_clamp_index(s, P, a.sys, dev->n_sys, w.sys, a.status));
+  const int32_t* sysc = w.sys;
+  const int32_t* erow = nullptr;
+  if (a.scatR && a.e_idx) {
+    CK(launch_clamp_index(s, P, a.e_idx, a.n_rows, w.erow, a.status));
+    erow = w.erow;
+  }
+  auto F = [&](z64* p) { return BM<double>{p, (long long)bb, nullptr, b}; };
+  auto Fc = [&](const z64* p) { return BMc<double>{p, (long long)bb, nullptr, b}; };
+  auto S = [&](z64* base, int i) { return base + (size_t)i * PB; };
+  auto Hd = [&](int i) {
+    return BMc<double>{reinterpret_cast<const z64*>(dev->H_diag) + (size_t)i * bb,
+                       (long long)(N * bb), sysc, b};
+  };
+  auto Hu = [&](int i) {
+    return BMc<double>{reinterpret_cast<const z64*>(dev->H_up) + (size_t)i * bb,
+                       (long long)((N - 1) * bb), sysc, b};
+  };
+  const BMc<double> SigL_R{a.sigR, (long long)(2 * bb), nullptr, b};
+  const BMc<double> SigR_R{a.sigR + bb, (long long)(2 * bb), nullptr, b};
+  const BMc<double> SigL_L{a.sigL, (long long)(2 * bb), nullptr, b};
+  const BMc<double> SigR_L{a.sigL + bb, (long long)(2 * bb), nullptr, b};
+  z64** T = w.t;
+  auto has_src = [&](int i) { return i == 0 || i == N - 1 || a.scatL != nullptr; };
+  auto build_src = [&](int i, z64* out) -> cudaError_t {
+    return launch_source(s, P, b, a.scatL ? a.scatL + (size_t)i * b : nullptr, NB, erow,
+                         i == 0 ? SigL_L : none, i == N - 1 ? SigR_L : none, F(out), nullptr);
+  };
+  const double eta = a.opt->eta_device;
+
+  // ------------------------------------------------ forward sweep (values kept)
+  for (int i = 0; i < N; ++i) {
+    BMc<double> Y = none;
+    if (i > 0) {
+      CK(eng.gemm(P, b, b, b, one, Fc(S(w.gF, i - 1)), OP_N, Hu(i - 1), OP_N, zero,
+                  F(S(w.Lb, i - 1)), zero, none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Hu(i - 1), OP_C, Fc(S(w.Lb, i - 1)), OP_N, zero, F(T[0]), zero,
+                  none, nullptr));
+      Y = Fc(T[0]);
+    }
+    CK(launch_assemble(s, P, b, a.E, eta, Hd(i), a.V ? a.V + (size_t)i * b : nullptr,
+                       a.scatR ? a.scatR + (size_t)i * b : nullptr, NB, erow, Y,
+                       i == 0 ? SigL_R : none, i == N - 1 ? SigR_R : none, F(T[1]), nullptr));
+    CK(eng.inv(P, F(T[1]), F(S(w.gF, i)), a.status, nullptr));
+    bool prev = false;
+    if (i > 0) {
+      CK(eng.gemm(P, b, b, b, one, Fc(S(w.gF, i)), OP_N, Hu(i - 1), OP_C, zero, F(T[2]), zero,
+                  none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(S(w.glF, i - 1)), OP_N, Fc(T[2]), OP_C, zero, F(T[3]), zero,
+                  none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(T[2]), OP_N, Fc(T[3]), OP_N, zero, F(S(w.glF, i)), zero,
+                  none, nullptr));
+      prev = true;
+    }
+    if (has_src(i)) {
+      CK(build_src(i, T[4]));
+      CK(eng.gemm(P, b, b, b, one, Fc(S(w.gF, i)), OP_N, Fc(T[4]), OP_N, zero, F(T[5]), zero,
+                  none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(T[5]), OP_N, Fc(S(w.gF, i)), OP_C, prev ? one : zero,
+                  F(S(w.glF, i)), zero, none, nullptr));
+    } else if (!prev) {
+      CK(cudaMemsetAsync(S(w.glF, i), 0, PB * sizeof(z64), s));
+    }
+  }
+  // ------------------------------------------------ backward sweep (into separate buffers)
+  CK(cudaMemcpyAsync(S(w.Gb, N - 1), S(w.gF, N - 1), PB * sizeof(z64), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(S(w.GLb, N - 1), S(w.glF, N - 1), PB * sizeof(z64), cudaMemcpyDeviceToDevice, s));
+  for (int i = N - 2; i >= 0; --i) {
+    z64 *Wm = T[0], *LW = T[1], *Q = T[2], *U = T[3];
+    CK(eng.gemm(P, b, b, b, one, Fc(S(w.Gb, i + 1)), OP_N, Hu(i), OP_C, zero, F(Wm), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(S(w.Lb, i)), OP_N, Fc(Wm), OP_N, zero, F(LW), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(LW), OP_N, Fc(S(w.gF, i)), OP_N, zero, F(S(w.Gb, i)), one,
+                Fc(S(w.gF, i)), nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(S(w.GLb, i + 1)), OP_N, Fc(S(w.Lb, i)), OP_C, zero, F(Q), zero,
+                none, nullptr));
+    CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_N, Fc(S(w.glF, i)), OP_N, zero, F(U), one, Fc(Q), nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(S(w.Lb, i)), OP_N, Fc(U), OP_N, zero, F(T[4]), one,
+                Fc(S(w.glF, i)), nullptr));
+    CK(launch_antiherm(s, P, b, Fc(T[4]), F(S(w.GLb, i)), nullptr));
+  }
+
+  // ------------------------------------------------ reverse of the backward sweep
+  CK(cudaMemsetAsync(w.gbar, 0, (size_t)N * PB * sizeof(z64), s));
+  CK(cudaMemsetAsync(w.glbar, 0, (size_t)N * PB * sizeof(z64), s));
+  CK(cudaMemsetAsync(w.Lbar, 0, (size_t)std::max(N - 1, 1) * PB * sizeof(z64), s));
+  CK(cudaMemsetAsync(w.Gc, 0, PB * sizeof(z64), s));
+  k_seed_density<<<g2((long long)bb, P), kT, 0, s>>>(b, 0, NB, a.nbar, F(w.GLc));
+  count_launch();
+  z64 *Gc = w.Gc, *Gn = w.Gn, *GLc = w.GLc, *GLn = w.GLn;
+  for (int i = 0; i + 1 < N; ++i) {
+    z64 *Wm = T[0], *LW = T[1], *Q = T[2], *U = T[3], *Sb = T[4], *Ub = T[5], *Wb = T[6],
+        *Qb = T[7], *LWb = T[8];
+    z64* L = S(w.Lb, i);
+    // recompute W, LW, Q, U of backward step i
+    CK(eng.gemm(P, b, b, b, one, Fc(S(w.Gb, i + 1)), OP_N, Hu(i), OP_C, zero, F(Wm), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(L), OP_N, Fc(Wm), OP_N, zero, F(LW), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(S(w.GLb, i + 1)), OP_N, Fc(L), OP_C, zero, F(Q), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_N, Fc(S(w.glF, i)), OP_N, zero, F(U), one, Fc(Q), nullptr));
+    // current cotangent: Ubar = Qbar = d_i t_i^H
+    k_set_dtH<<<g2((long long)bb, P), kT, 0, s>>>(b, Hu(i), a.jbar ? a.jbar + i : nullptr, N - 1, F(Ub));
+    k_set_dtH<<<g2((long long)bb, P), kT, 0, s>>>(b, Hu(i), a.jbar ? a.jbar + i : nullptr, N - 1, F(Qb));
+    count_launch(2);
+    // G^<_i = AH(g^<_i + L U)
+    CK(launch_antiherm(s, P, b, Fc(GLc), F(Sb), nullptr));
+    k_axpy<<<(unsigned)std::min<size_t>((PB + kT - 1) / kT, 4096), kT, 0, s>>>((long long)PB, Sb, S(w.glbar, i));
+    count_launch();
+    CK(eng.gemm(P, b, b, b, one, Fc(Sb), OP_N, Fc(U), OP_C, one, F(S(w.Lbar, i)), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(L), OP_C, Fc(Sb), OP_N, one, F(Ub), zero, none, nullptr));
+    // U = 2 W g^<_i + Q
+    CK(eng.gemm(P, b, b, b, two, Fc(Ub), OP_N, Fc(S(w.glF, i)), OP_C, zero, F(Wb), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_C, Fc(Ub), OP_N, one, F(S(w.glbar, i)), zero, none, nullptr));
+    k_axpy<<<(unsigned)std::min<size_t>((PB + kT - 1) / kT, 4096), kT, 0, s>>>((long long)PB, Ub, Qb);
+    count_launch();
+    // Q = G^<_{i+1} L^H
+    k_seed_density<<<g2((long long)bb, P), kT, 0, s>>>(b, i + 1, NB, a.nbar, F(GLn));
+    count_launch();
+    CK(eng.gemm(P, b, b, b, one, Fc(Qb), OP_N, Fc(L), OP_N, one, F(GLn), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(Qb), OP_C, Fc(S(w.GLb, i + 1)), OP_N, one, F(S(w.Lbar, i)), zero,
+                none, nullptr));
+    // G_i = g_i + LW g_i
+    k_axpy<<<(unsigned)std::min<size_t>((PB + kT - 1) / kT, 4096), kT, 0, s>>>((long long)PB, Gc, S(w.gbar, i));
+    count_launch();
+    CK(eng.gemm(P, b, b, b, one, Fc(Gc), OP_N, Fc(S(w.gF, i)), OP_C, zero, F(LWb), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(LW), OP_C, Fc(Gc), OP_N, one, F(S(w.gbar, i)), zero, none, nullptr));
+    // LW = L W
+    CK(eng.gemm(P, b, b, b, one, Fc(LWb), OP_N, Fc(Wm), OP_C, one, F(S(w.Lbar, i)), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(L), OP_C, Fc(LWb), OP_N, one, F(Wb), zero, none, nullptr));
+    // W = G_{i+1} t_i^H
+    CK(eng.gemm(P, b, b, b, one, Fc(Wb), OP_N, Hu(i), OP_N, zero, F(Gn), zero, none, nullptr));
+    std::swap(Gc, Gn);
+    std::swap(GLc, GLn);
+  }
+  // slab N-1: G = g, G^< = g^< directly
+  k_axpy<<<(unsigned)std::min<size_t>((PB + kT - 1) / kT, 4096), kT, 0, s>>>((long long)PB, Gc, S(w.gbar, N - 1));
+  k_axpy<<<(unsigned)std::min<size_t>((PB + kT - 1) / kT, 4096), kT, 0, s>>>((long long)PB, GLc, S(w.glbar, N - 1));
+  count_launch(2);
+
+  // ------------------------------------------------ reverse of the forward sweep
+  for (int i = N - 1; i >= 0; --i) {
+    z64 *K = T[0], *Vt = T[1], *Kb = T[2], *Vtb = T[3], *Ssrc = T[4], *Wsrc = T[5], *Wbar = T[6],
+        *T1 = T[7], *Mb = T[8];
+    z64* gb = S(w.gbar, i);
+    z64* glb = S(w.glbar, i);
+    if (i > 0) {
+      CK(eng.gemm(P, b, b, b, one, Fc(S(w.gF, i)), OP_N, Hu(i - 1), OP_C, zero, F(K), zero, none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(S(w.glF, i - 1)), OP_N, Fc(K), OP_C, zero, F(Vt), zero, none, nullptr));
+      // g^<_i = K Vt (+ source)
+      CK(eng.gemm(P, b, b, b, one, Fc(glb), OP_N, Fc(Vt), OP_C, zero, F(Kb), zero, none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(K), OP_C, Fc(glb), OP_N, zero, F(Vtb), zero, none, nullptr));
+      // Vt = g^<_{i-1} K^H
+      CK(eng.gemm(P, b, b, b, one, Fc(Vtb), OP_C, Fc(S(w.glF, i - 1)), OP_N, one, F(Kb), zero, none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(Vtb), OP_N, Fc(K), OP_N, one, F(S(w.glbar, i - 1)), zero, none,
+                  nullptr));
+      // K = g_i t_{i-1}^H
+      CK(eng.gemm(P, b, b, b, one, Fc(Kb), OP_N, Hu(i - 1), OP_N, one, F(gb), zero, none, nullptr));
+    }
+    if (has_src(i)) {
+      CK(build_src(i, Ssrc));
+      CK(eng.gemm(P, b, b, b, one, Fc(S(w.gF, i)), OP_N, Fc(Ssrc), OP_N, zero, F(Wsrc), zero, none, nullptr));
+      // g^<_i += Wsrc g_i^H
+      CK(eng.gemm(P, b, b, b, one, Fc(glb), OP_N, Fc(S(w.gF, i)), OP_N, zero, F(Wbar), zero, none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(glb), OP_C, Fc(Wsrc), OP_N, one, F(gb), zero, none, nullptr));
+      // Wsrc = g_i S
+      CK(eng.gemm(P, b, b, b, one, Fc(Wbar), OP_N, Fc(Ssrc), OP_C, one, F(gb), zero, none, nullptr));
+    }
+    // g_i = M_i^-1:  Mbar = -g^H gbar g^H
+    CK(eng.gemm(P, b, b, b, one, Fc(gb), OP_N, Fc(S(w.gF, i)), OP_C, zero, F(T1), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, mone, Fc(S(w.gF, i)), OP_C, Fc(T1), OP_N, zero, F(Mb), zero, none, nullptr));
+    k_vbar<<<g2(b, P), kT, 0, s>>>(b, i, NB, Fc(Mb), w.vb);
+    count_launch();
+    if (i > 0) {
+      // M_i = ... - t^H L_{i-1}:  Lbar_{i-1} -= t Mbar;  L_{i-1} = g_{i-1} t
+      CK(eng.gemm(P, b, b, b, mone, Hu(i - 1), OP_N, Fc(Mb), OP_N, one, F(S(w.Lbar, i - 1)), zero,
+                  none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(S(w.Lbar, i - 1)), OP_N, Hu(i - 1), OP_C, one,
+                  F(S(w.gbar, i - 1)), zero, none, nullptr));
+    }
+  }
+  k_sum_points<<<(NB + kT - 1) / kT, kT, 0, s>>>(P, NB, w.vb, a.Vbar, a.accumulate ? 1 : 0);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
+}
+
+constexpr size_t kAdjBudget = 32ull << 30;
+
+}  // namespace
+
 size_t adjoint_bytes(const negf_device* dev, int P, const negf_options* opt) {
-  (void)dev; (void)P; (void)opt;
-  return 0;
+  size_t off = 0;
+  AdjWs w;
+  carve_adj(nullptr, off, P, dev->block, dev->n_slabs, opt->precision, w);
+  return off + 256;
 }
+
 int adjoint_chunk(const negf_device* dev, int n_pts, const negf_options* opt) {
-  (void)dev; (void)opt;
-  return n_pts < 1 ? 1 : n_pts;
+  if (opt->chunk > 0) return std::max(1, std::min(std::min(opt->chunk, n_pts), 16384));
+  const size_t per = adjoint_bytes(dev, 2, opt) - adjoint_bytes(dev, 1, opt);
+  size_t c = std::max<size_t>(1, kAdjBudget / std::max<size_t>(per, 1));
+  return (int)std::max<size_t>(1, std::min<size_t>(c, (size_t)std::max(n_pts, 1)));
 }
+
 }  // namespace negf
 
-extern "C" negf_status negf_rgf_adjoint(const negf_device*, int32_t, const double*,
-                                        const int32_t*, const double*, const double*,
-                                        const double*, const double*, const double*,
-                                        const int32_t*, int32_t, const negf_options*,
-                                        const double*,
-                                        const double*, double*, int32_t*, void*, size_t, void*) {
-  return NEGF_ERR_UNSUPPORTED;
+using namespace negf;
+
+extern "C" negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, const double* E,
+                                        const int32_t* sys_idx, const double* V,
+                                        const double* sigma_R, const double* sigma_L,
+                                        const double* scat_R, const double* scat_L,
+                                        const int32_t* e_idx, int32_t n_rows,
+                                        const negf_options* opt, const double* density_bar,
+                                        const double* current_bar, double* V_bar,
+                                        int32_t* status, void* ws, size_t ws_bytes,
+                                        void* stream) {
+  if (!dev || !opt || dev->n_sys < 1 || dev->n_slabs < 1 || dev->block < 1 || !dev->H_diag ||
+      (dev->n_slabs > 1 && !dev->H_up) || n_pts < 0)
+    return NEGF_ERR_ARG;
+  if (!engine_supports(opt->precision)) return NEGF_ERR_UNSUPPORTED;
+  if (!(opt->kT > 0.0) || opt->refine_steps < 0 || opt->refine_steps > 8 || opt->chunk < 0)
+    return NEGF_ERR_ARG;
+  if (!V_bar) return NEGF_ERR_ARG;
+  const int b = dev->block, N = dev->n_slabs;
+  const size_t NB = (size_t)N * b;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (n_pts == 0) {
+    return cudaMemsetAsync(V_bar, 0, NB * sizeof(double), s) == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
+  }
+  if (!E || !sys_idx || !sigma_R || !sigma_L || !status) return NEGF_ERR_ARG;
+  if ((scat_R == nullptr) != (scat_L == nullptr)) return NEGF_ERR_ARG;
+  if (scat_R && (e_idx ? n_rows < 1 : n_rows < n_pts)) return NEGF_ERR_ARG;
+  const int C = adjoint_chunk(dev, n_pts, opt);
+  if (!ws || ws_bytes < adjoint_bytes(dev, C, opt)) return NEGF_ERR_NOMEM;
+  if (cudaMemsetAsync(status, 0, (size_t)n_pts * sizeof(int32_t), s) != cudaSuccess)
+    return NEGF_ERR_CUDA;
+  const size_t bb = (size_t)b * b;
+  for (int p0 = 0; p0 < n_pts; p0 += C) {
+    const int P = std::min(C, n_pts - p0);
+    AdjArgs a;
+    a.dev = dev;
+    a.E = E + p0;
+    a.sys = sys_idx + p0;
+    a.V = V;
+    a.sigR = reinterpret_cast<const z64*>(sigma_R) + (size_t)p0 * 2 * bb;
+    a.sigL = reinterpret_cast<const z64*>(sigma_L) + (size_t)p0 * 2 * bb;
+    a.e_idx = e_idx ? e_idx + p0 : nullptr;
+    a.n_rows = n_rows;
+    a.scatR = scat_R ? reinterpret_cast<const z64*>(scat_R) + (e_idx ? 0 : (size_t)p0 * NB) : nullptr;
+    a.scatL = scat_L ? reinterpret_cast<const z64*>(scat_L) + (e_idx ? 0 : (size_t)p0 * NB) : nullptr;
+    a.opt = opt;
+    a.nbar = density_bar ? density_bar + (size_t)p0 * NB : nullptr;
+    a.jbar = (current_bar && N > 1) ? current_bar + (size_t)p0 * (N - 1) : nullptr;
+    a.Vbar = V_bar;
+    a.accumulate = p0 > 0;
+    a.status = status + p0;
+    negf_status r = adjoint_chunk_run(a, P, static_cast<char*>(ws), s);
+    if (r != NEGF_OK) return r;
+  }
+  return NEGF_OK;
 }

@@ -373,3 +373,36 @@ def profile_read(kind=PROF_TC_GEMM):
 
 def launch_count() -> int:
     return int(library().negf_launch_count())
+
+
+class RGFFunction(torch.autograd.Function):
+    """(density [n, N*b], current [n, N-1]) = RGF(V [N, b]) with a hand-written adjoint.
+
+    Forward runs negf_rgf_solve; backward runs negf_rgf_adjoint with the incoming cotangents, so
+    autograd returns dL/dV for any scalar L built from the density and current (the gradient a
+    Newton-Poisson loop needs).  Lead and scattering self-energies are held fixed."""
+
+    @staticmethod
+    def forward(ctx, V, dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R=None, scat_L=None,
+                e_idx=None):
+        out = rgf_solve(dev, E, sys_idx, sigma_R, sigma_L, opt, V=V.detach().contiguous(),
+                        scat_R=scat_R, scat_L=scat_L, e_idx=e_idx,
+                        outputs=("density", "current"))
+        ctx.args = (dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R, scat_L, e_idx)
+        ctx.save_for_backward(V.detach())
+        return out["density"], out["current"]
+
+    @staticmethod
+    def backward(ctx, g_density, g_current):
+        (V,) = ctx.saved_tensors
+        dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R, scat_L, e_idx = ctx.args
+        gd = None if g_density is None else g_density.contiguous()
+        gc = None if g_current is None else g_current.contiguous()
+        Vbar, _ = rgf_adjoint(dev, E, sys_idx, sigma_R, sigma_L, opt, density_bar=gd,
+                              current_bar=gc, V=V, scat_R=scat_R, scat_L=scat_L, e_idx=e_idx)
+        return (Vbar,) + (None,) * 9
+
+
+def rgf(V, dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R=None, scat_L=None, e_idx=None):
+    """Differentiable (density, current) of the points with respect to V."""
+    return RGFFunction.apply(V, dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R, scat_L, e_idx)
