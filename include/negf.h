@@ -246,6 +246,16 @@ negf_status negf_zinv_batched(int32_t precision, int32_t n_batch, int32_t n, dou
 negf_status negf_zinv_batched_noalloc(int32_t n_batch, int32_t n, double* M, double* X,
                                       int32_t* status, void* stream);
 
+/* ---- tensor-core GEMM configuration (autotuning) ----------------------------------------
+ * The mixed-precision GEMM has negf_tc_config_count() kernel configurations, differing only in
+ * speed: configuration c uses (4, 6, 7)[c / 2] pipeline stages and splits K into at most
+ * (4, 8)[c % 2] exactly accumulated parts (more parts allow wider slices and fewer slice
+ * products).  negf_tc_config_set selects one process-wide (default 2); results agree to the
+ * GEMM's rounding.  The package's autotuner times them per block size and stores the choice. */
+int32_t negf_tc_config_count(void);
+negf_status negf_tc_config_set(int32_t idx);
+int32_t negf_tc_config_get(void);
+
 /* ---- accounting ----------------------------------------------------------------------------
  * Instrumentation for benchmarks, not part of the method.  negf_launch_count() is the number
  * of kernels this library has launched since it was loaded.  With profiling on, every launch of

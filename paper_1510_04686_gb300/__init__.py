@@ -20,6 +20,8 @@ from .negf import (  # noqa: F401
     launch_count,
     PROF_TC_GEMM,
     RGFFunction,
+    tc_config,
+    tc_config_count,
     rgf,
     PROF_SLICE,
     workspace_size,

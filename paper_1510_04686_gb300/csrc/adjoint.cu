@@ -151,7 +151,7 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   size_t off = 0;
   AdjWs w;
   carve_adj(wsbase, off, P, b, N, a.opt->precision, w);
-  Engine eng(s, a.opt, w.eng, b);
+  Engine eng(s, a.opt, w.eng, b, dev->n_sys);
   CK(launch_clamp_index(s, P, a.sys, dev->n_sys, w.sys, a.status));
   const int32_t* sysc = w.sys;
   const int32_t* erow = nullptr;

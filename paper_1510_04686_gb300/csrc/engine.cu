@@ -87,7 +87,7 @@ cudaError_t Engine::gemm(int P, int M, int N, int K, z64 alpha, BMc<double> A, i
                          BMc<double> D, const int32_t* active) {
   if (opt->precision == NEGF_PREC_MIXED)
     return tc_gemm(s, P, M, N, K, alpha, A, opA, B, opB, beta, C, gamma, D, false, active,
-                   tc_view(w, P, b));
+                   tc_view(w, P, b), n_sys);
   return gemm_simt<double>(s, P, M, N, K, alpha, A, opA, B, opB, beta, C, gamma, D, active);
 }
 

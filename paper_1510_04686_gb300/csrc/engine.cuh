@@ -34,8 +34,9 @@ struct Engine {
   const negf_options* opt;
   EngineWs w;
   int b;
-  Engine(cudaStream_t s_, const negf_options* o, const EngineWs& w_, int b_)
-      : s(s_), opt(o), w(w_), b(b_) {}
+  int n_sys = 0;  // distinct Hamiltonians an indexed operand selects from (0 = unknown)
+  Engine(cudaStream_t s_, const negf_options* o, const EngineWs& w_, int b_, int n_sys_ = 0)
+      : s(s_), opt(o), w(w_), b(b_), n_sys(n_sys_) {}
   // C = alpha op(A) op(B) + beta C + gamma D for P batch items of M x N x K.
   cudaError_t gemm(int P, int M, int N, int K, z64 alpha, BMc<double> A, int opA, BMc<double> B,
                    int opB, z64 beta, BM<double> C, z64 gamma, BMc<double> D,

@@ -159,7 +159,7 @@ negf_status lead_chunk_run(const negf_device* dev, int P, const double* E, const
   Carver c{wsbase, 0};
   LeadWs w;
   carve_lead(c, P, b, opt, w);
-  Engine eng(s, opt, w.eng, b);
+  Engine eng(s, opt, w.eng, b, dev->n_sys);
   CK(launch_clamp_index(s, P, sys_in, dev->n_sys, w.sys, status));
   const int32_t* sys = w.sys;
   BMc<double> Hd{reinterpret_cast<const z64*>(dev->H_diag), (long long)(N * bb), sys, b};
@@ -253,7 +253,7 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
   Carver c{wsbase, 0};
   RgfWs w;
   carve_rgf(c, P, b, N, a.opt, w);
-  Engine eng(s, a.opt, w.eng, b);
+  Engine eng(s, a.opt, w.eng, b, dev->n_sys);
   const double eta = a.opt->eta_device;
   CK(launch_clamp_index(s, P, a.sys, dev->n_sys, w.sys, a.status));
   const int32_t* sysc = w.sys;

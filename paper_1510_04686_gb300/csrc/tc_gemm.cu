@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -17,17 +18,21 @@ namespace {
 
 constexpr int kBM = 128;      // tile rows = TMEM lanes
 constexpr int kKC = 64;       // real K elements per stage (128 bytes of BF16 per row)
-constexpr int kStages = 4;
-constexpr int kMaxItems = 96;
-constexpr int kThreads = 192;  // warps 0-3 epilogue, warp 4 TMA producer, warp 5 MMA issuer
+constexpr int kMaxItems = 240;
+constexpr int kThreads = 320;  // warps 0-7 epilogue, warp 8 TMA producer, warp 9 MMA issuer
+constexpr int kEpiWarps = 8;
+constexpr int kNT = 128;       // tile columns (real); TMEM: 2 accumulators + FP32-pair sums
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on every device wait
 
+constexpr int kMaxParts = 8;
 struct Item {
-  int8_t acc, s, t0, nt;  // accumulator group, A slice, first B slice, number of B slices
+  int8_t acc, s, t, kp;  // accumulator group, A slice, B slice, K part
 };
 struct Sched {
   int n_items;
   int n_acc;
+  int part_lo[kMaxParts];  // first K chunk of each part
+  int part_hi[kMaxParts];  // one past the last K chunk
   Item it[kMaxItems];
 };
 
@@ -116,18 +121,50 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+
+// 32 consecutive TMEM columns of this warp's lane quarter, no wait (tcgen05.wait::ld follows)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32"
-      " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32"
+      " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
       : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32"
+      " [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+// (double)x * 2^k from the bit pattern of the FP32 number x with integer operations only
+// (exact; x normal or zero, result in the normal double range).  FP64 arithmetic is scarce on
+// this GPU, so the epilogue converts without cvt/mul.
+__device__ __forceinline__ double f32_scaled(uint32_t xb, int k) {
+  const uint32_t ex = (xb >> 23) & 0xFFu;
+  if (ex == 0u) return 0.0;  // zero (FP32 subnormals do not occur: slices are integers x 2^-n)
+  const unsigned long long sign = (unsigned long long)(xb >> 31) << 63;
+  const unsigned long long e64 = (unsigned long long)(ex + (1023 - 127) + k) << 52;
+  const unsigned long long man = (unsigned long long)(xb & 0x7FFFFFu) << 29;
+  return __longlong_as_double((long long)(sign | e64 | man));
+}
+
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ slicing kernels
@@ -137,12 +174,6 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
-__device__ __forceinline__ z64 opelem(const z64* a, int ld, int op, int r, int c) {
-  if (op == OP_N) return a[(long long)r * ld + c];
-  z64 v = a[(long long)c * ld + r];
-  if (op == OP_C) v.im = -v.im;
-  return v;
-}
 
 // |x| as an ordered integer (the bit pattern without the sign)
 __device__ __forceinline__ unsigned long long absbits(double x) {
@@ -191,92 +222,125 @@ __device__ __forceinline__ void cut(double x, int e, int S, int beta, float* out
 
 constexpr int kMaxS = 12;
 
-// A' rows: [Re, Im] interleaved along K.  One warp per row of op(A).
-__global__ void k_slice_a(int M, int K, int L, int S, int beta, BMc<double> A, int opA,
-                          __nv_bfloat16* out, int32_t* eo, const int32_t* active) {
+// Slicing of 32 "lines" per CTA (rows of op(A), or columns of op(B)) with coalesced reads: the
+// operand is read in 32 x 32 complex tiles through shared memory, so a line that is a column in
+// memory costs the same as a row.  Pass 1 finds each line's scale exponent, pass 2 writes the S
+// slices.  A lines become one output row [Re, Im, Re, Im, ...]; B lines (columns n of op(B))
+// become the two rows 2n = [Re, -Im, ...] and 2n + 1 = [Im, Re, ...] of the real embedding.
+template <bool kB>
+__global__ void __launch_bounds__(256) k_slice(int n_lines, int K, int L, int S, int beta,
+                                               BMc<double> X, int op, bool line_is_col,
+                                               __nv_bfloat16* out, int32_t* eo,
+                                               const int32_t* active) {
   const int p = blockIdx.y;
   if (active && !active[p]) return;
+  __shared__ z64 tile[32][33];
+  __shared__ int sexp[32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m = blockIdx.x * (blockDim.x >> 5) + w;
-  if (m >= M) return;
-  const z64* a = bat(A, p);
-  unsigned long long mb = 0;
-  for (int k = lane; k < K; k += 32) {
-    z64 v = opelem(a, A.ld, opA, m, k);
-    mb = max(mb, absbits(v.re));
-    mb = max(mb, absbits(v.im));
+  const int l0 = blockIdx.x * 32;
+  const z64* x = bat(X, p);
+  const long long ld = X.ld;
+  const bool conj = (op == OP_C);
+  auto load_tile = [&](int k0) {
+    // 32 lines x 32 k values; lanes run along the contiguous index of memory
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      const int a = e >> 5, bidx = e & 31;  // a: slow index, bidx: fast (contiguous) index
+      int li, k;
+      if (line_is_col) {
+        k = a;
+        li = bidx;  // memory x[k][line]
+      } else {
+        li = a;
+        k = bidx;   // memory x[line][k]
+      }
+      const int line = l0 + li, kk = k0 + k;
+      z64 v = mkc(0.0, 0.0);
+      if (line < n_lines && kk < K)
+        v = line_is_col ? x[(long long)kk * ld + line] : x[(long long)line * ld + kk];
+      tile[li][k] = v;
+    }
+  };
+  unsigned long long mb[4] = {0, 0, 0, 0};
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    load_tile(k0);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const z64 v = tile[w + 8 * j][lane];
+      mb[j] = max(mb[j], max(absbits(v.re), absbits(v.im)));
+    }
+    __syncthreads();
   }
-  mb = warp_max(mb);
-  const int e = scale_exp(__longlong_as_double((long long)mb));
-  if (lane == 0) eo[(long long)p * M + m] = e;
-  float sr[kMaxS], si[kMaxS];
-  for (int k2 = lane; k2 < L / 2; k2 += 32) {
-    z64 v = (k2 < K) ? opelem(a, A.ld, opA, m, k2) : mkc(0.0, 0.0);
-    cut(v.re, e, S, beta, sr);
-    cut(v.im, e, S, beta, si);
-    for (int s = 0; s < S; ++s) {
-      __nv_bfloat162 pr;
-      pr.x = __float2bfloat16_rn(sr[s]);
-      pr.y = __float2bfloat16_rn(si[s]);
-      reinterpret_cast<__nv_bfloat162*>(out + (((long long)p * S + s) * M + m) * L)[k2] = pr;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const unsigned long long m = warp_max(mb[j]);
+    const int line = l0 + w + 8 * j;
+    if (lane == 0) {
+      const int e = scale_exp(__longlong_as_double((long long)m));
+      sexp[w + 8 * j] = e;
+      if (line < n_lines) eo[(long long)p * n_lines + line] = e;
     }
   }
-}
-
-// B'^T rows 2n (= [Re, -Im]) and 2n + 1 (= [Im, Re]) from column n of op(B).
-__global__ void k_slice_b(int K, int N, int L, int S, int beta, BMc<double> B, int opB,
-                          __nv_bfloat16* out, int32_t* fo, const int32_t* active) {
-  const int p = blockIdx.y;
-  if (active && !active[p]) return;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n = blockIdx.x * (blockDim.x >> 5) + w;
-  if (n >= N) return;
-  const z64* b = bat(B, p);
-  unsigned long long mb = 0;
-  for (int k = lane; k < K; k += 32) {
-    z64 v = opelem(b, B.ld, opB, k, n);
-    mb = max(mb, absbits(v.re));
-    mb = max(mb, absbits(v.im));
-  }
-  mb = warp_max(mb);
-  const int f = scale_exp(__longlong_as_double((long long)mb));
-  if (lane == 0) fo[(long long)p * N + n] = f;
-  const long long N2 = 2LL * N;
+  __syncthreads();
+  const long long rows_out = kB ? 2LL * n_lines : (long long)n_lines;
   float sr[kMaxS], si[kMaxS];
-  for (int k2 = lane; k2 < L / 2; k2 += 32) {
-    z64 v = (k2 < K) ? opelem(b, B.ld, opB, k2, n) : mkc(0.0, 0.0);
-    cut(v.re, f, S, beta, sr);
-    cut(v.im, f, S, beta, si);
-    for (int s = 0; s < S; ++s) {
-      __nv_bfloat16* base = out + ((long long)p * S + s) * N2 * L;
-      __nv_bfloat162 r0, r1;
-      r0.x = __float2bfloat16_rn(sr[s]);
-      r0.y = __float2bfloat16_rn(-si[s]);
-      r1.x = __float2bfloat16_rn(si[s]);
-      r1.y = __float2bfloat16_rn(sr[s]);
-      reinterpret_cast<__nv_bfloat162*>(base + (2LL * n) * L)[k2] = r0;
-      reinterpret_cast<__nv_bfloat162*>(base + (2LL * n + 1) * L)[k2] = r1;
+  for (int k0 = 0; k0 < L / 2; k0 += 32) {
+    if (k0 < K) load_tile(k0);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int li = w + 8 * j, line = l0 + li;
+      const int k2 = k0 + lane;
+      if (line >= n_lines) continue;
+      z64 v = (k0 < K) ? tile[li][lane] : mkc(0.0, 0.0);
+      if (conj) v.im = -v.im;
+      const int e = sexp[li];
+      cut(v.re, e, S, beta, sr);
+      cut(v.im, e, S, beta, si);
+      for (int s = 0; s < S; ++s) {
+        __nv_bfloat16* base = out + ((long long)p * S + s) * rows_out * L;
+        if (!kB) {
+          __nv_bfloat162 pr;
+          pr.x = __float2bfloat16_rn(sr[s]);
+          pr.y = __float2bfloat16_rn(si[s]);
+          reinterpret_cast<__nv_bfloat162*>(base + (long long)line * L)[k2] = pr;
+        } else {
+          __nv_bfloat162 r0, r1;
+          r0.x = __float2bfloat16_rn(sr[s]);
+          r0.y = __float2bfloat16_rn(-si[s]);
+          r1.x = __float2bfloat16_rn(si[s]);
+          r1.y = __float2bfloat16_rn(sr[s]);
+          reinterpret_cast<__nv_bfloat162*>(base + (2LL * line) * L)[k2] = r0;
+          reinterpret_cast<__nv_bfloat162*>(base + (2LL * line + 1) * L)[k2] = r1;
+        }
+      }
     }
+    __syncthreads();
   }
 }
 
 // ------------------------------------------------------------------ MMA kernel
-template <int NT, int MAXT>
+template <int NT, int STAGES>
 struct Cfg {
+  static constexpr int kStages = STAGES;
   static constexpr int kATile = kBM * kKC * 2;                // 16 KB
   static constexpr int kBTile = NT * kKC * 2;
-  static constexpr int kStage = kATile + MAXT * kBTile;
+  static constexpr int kStage = kATile + kBTile;
   static constexpr int kSmem = kStages * kStage + 1024 + 256;  // + alignment + barriers
 };
 
-template <int NT, int MAXT>
+template <int NT, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-              const Sched sched, int M, int N2, int L, int S, int two_beta,
-              const int32_t* __restrict__ eA, const int32_t* __restrict__ fB, double* T64,
-              z64 alpha, z64 beta, z64 gamma, BM<double> C, BMc<double> D, int add_identity,
+              const Sched sched, int M, int N2, int S, int two_beta,
+              const int32_t* __restrict__ eA, const int32_t* __restrict__ fB,
+              const int32_t* __restrict__ zidxA, int zmodeA, const int32_t* __restrict__ zidxB,
+              int zmodeB, z64 alpha,
+              z64 beta, z64 gamma, BM<double> C, BMc<double> D, int add_identity,
               const int32_t* active, int32_t* err) {
-  using CF = Cfg<NT, MAXT>;
+  static_assert(NT == 128, "TMEM holds 2 x NT accumulator columns + 2 x NT sum columns");
+  using CF = Cfg<NT, STAGES>;
+  constexpr int kStages = CF::kStages;
   const int p = blockIdx.z;
   if (active && !active[p]) return;
   extern __shared__ unsigned char smem_raw[];
@@ -291,7 +355,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * NT, m0 = blockIdx.y * kBM;
-  const int nk = L / kKC;
+  // slice set of this batch item: its own (mode 0), the indexed one (1) or the shared one (2)
+  const int zA = zmodeA == 0 ? p : (zmodeA == 1 ? zidxA[p] : 0);
+  const int zB = zmodeB == 0 ? p : (zmodeB == 1 ? zidxB[p] : 0);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
@@ -300,12 +366,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&accfull[i], 1);
-      mbar_init(&accempty[i], 4 * 32);
+      mbar_init(&accempty[i], kEpiWarps * 32);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 5) {
+  if (warp == 9) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      smem_u32(tmem_slot))
                  : "memory");
@@ -316,29 +382,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
-    // ---------------- TMA producer
+  if (warp == 8) {
+    // ---------------- TMA producer: for every item, the K chunks of its part
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
       for (int ii = 0; ii < sched.n_items && !*abort_flag; ++ii) {
         const Item it = sched.it[ii];
-        for (int kc = 0; kc < nk; ++kc) {
+        for (int kc = sched.part_lo[it.kp]; kc < sched.part_hi[it.kp]; ++kc) {
           if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
           unsigned char* st = smem + stage * CF::kStage;
-          mbar_expect_tx(&full[stage], CF::kATile + it.nt * CF::kBTile);
-          tma_load_3d(st, &mapA, &full[stage], kc * kKC, m0, p * S + it.s - 1);
-          for (int j = 0; j < it.nt; ++j)
-            tma_load_3d(st + CF::kATile + j * CF::kBTile, &mapB, &full[stage], kc * kKC, n0,
-                        p * S + it.t0 + j - 1);
+          mbar_expect_tx(&full[stage], CF::kATile + CF::kBTile);
+          tma_load_3d(st, &mapA, &full[stage], kc * kKC, m0, zA * S + it.s - 1);
+          tma_load_3d(st + CF::kATile, &mapB, &full[stage], kc * kKC, n0, zB * S + it.t - 1);
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1;
           }
         }
       }
-      // drain: wait (bounded) until the loads still in flight have landed
-      for (int i = 0; i < kStages; ++i) {
+      for (int i = 0; i < kStages; ++i) {  // drain loads still in flight (bounded)
         if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
         if (++stage == kStages) {
           stage = 0;
@@ -346,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     // ---------------- MMA issuer
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(kBM, NT);
@@ -367,7 +430,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const uint32_t dcol = tmem + (uint32_t)(buf * NT);
         bool ok = true;
-        for (int kc = 0; kc < nk; ++kc) {
+        for (int kc = sched.part_lo[it.kp]; kc < sched.part_hi[it.kp]; ++kc) {
           if (!mbar_wait(&full[stage], phase, abort_flag)) {
             ok = false;
             break;
@@ -376,12 +439,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a0 = smem_u32(smem + stage * CF::kStage);
 #pragma unroll
           for (int k = 0; k < kKC / 16; ++k) {
-            const uint64_t ad = sw128_desc(a0 + 32 * k);
-            for (int j = 0; j < it.nt; ++j) {
-              const uint64_t bd = sw128_desc(a0 + CF::kATile + j * CF::kBTile + 32 * k);
-              mma_bf16(dcol, ad, bd, idesc, acc_on);
-              acc_on = 1;
-            }
+            mma_bf16(dcol, sw128_desc(a0 + 32 * k), sw128_desc(a0 + CF::kATile + 32 * k), idesc,
+                     acc_on);
+            acc_on = 1;
           }
           mma_commit(&empty[stage]);
           if (++stage == kStages) {
@@ -395,57 +455,69 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- epilogue (warps 0-3 own TMEM lanes 32 w .. 32 w + 31)
-    // Every group value is exact in FP32; the running sum over groups is kept as an unevaluated
-    // pair hi + lo of FP32 numbers (TwoSum, renormalised), so FP64 arithmetic is needed only
-    // once per output, when the pair is scaled back and combined with C and D.
-    const int r = warp * 32 + lane;
+    // ---------------- epilogue: warp w owns TMEM lanes 32 (w % 4) .. + 31 (tile rows) and the
+    // 64 columns starting at 64 (w / 4).  Each exact group value is added to a running sum kept
+    // in TMEM as an unevaluated pair hi + lo of FP32 numbers (TwoSum, renormalised); FP64 is
+    // used once per output at the end.
+    const int q = warp & 3, half = warp >> 2;
+    const int r = q * 32 + lane;
     const int m = m0 + r;
     const bool row_ok = m < M;
-    const int em = row_ok ? eA[(long long)p * M + m] : 0;
+    const int em = row_ok ? eA[(long long)zA * M + m] : 0;
     const int N = N2 >> 1;
-    float2* trow = reinterpret_cast<float2*>(T64) + ((long long)p * M + (row_ok ? m : 0)) * N2;
+    const int32_t* fBp = fB + (long long)zB * N;
     z64* crow = row_ok ? bat(C, p) + (long long)m * C.ld : nullptr;
     const z64* drow = (row_ok && D.p) ? bat(D, p) + (long long)m * D.ld : nullptr;
     const bool use_beta = (beta.re != 0.0 || beta.im != 0.0);
     const bool unit_alpha = (alpha.re == 1.0 && alpha.im == 0.0);
     const bool unit_gamma = (gamma.re == 1.0 && gamma.im == 0.0);
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const int cbase = half * (NT / 2);
+    const uint32_t t_hi = tmem + lane_off + 2 * NT, t_lo = tmem + lane_off + 3 * NT;
     for (int acc = 0; acc < sched.n_acc; ++acc) {
       const int buf = acc & 1;
       if (!mbar_wait(&accfull[buf], (acc >> 1) & 1, abort_flag)) break;
       tc_fence_after();
       const bool last = (acc == sched.n_acc - 1);
-      for (int c0 = 0; c0 < NT; c0 += 16) {
-        float v[16];
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * NT + c0), v);
-        if (!row_ok) continue;
-        float lv[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + j;
-          if (col >= N2) break;
-          float hi = v[j], lo = 0.0f;
-          if (acc > 0) {
-            const float2 t = trow[col];
-            const float s1 = t.x + v[j];
-            const float bp = s1 - t.x;
-            const float err = (t.x - (s1 - bp)) + (v[j] - bp);
-            const float l1 = t.y + err;
-            hi = s1 + l1;
-            lo = l1 - (hi - s1);
-          }
-          if (!last) trow[col] = make_float2(hi, lo);
-          v[j] = hi;
-          lv[j] = lo;
+      for (int c0 = cbase; c0 < cbase + NT / 2; c0 += 32) {
+        uint32_t v[32], h[32], l[32];
+        tmem_ld32(tmem + lane_off + (uint32_t)(buf * NT + c0), v);
+        if (acc > 0) {
+          tmem_ld32(t_hi + c0, h);
+          tmem_ld32(t_lo + c0, l);
         }
-        if (last) {
+        tmem_ld_wait();
+        if (acc == 0) {
 #pragma unroll
-          for (int j = 0; j < 16; j += 2) {
+          for (int j = 0; j < 32; ++j) {
+            h[j] = v[j];
+            l[j] = 0u;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float hj = __uint_as_float(h[j]), vj = __uint_as_float(v[j]);
+            const float s1 = hj + vj;
+            const float bp = s1 - hj;
+            const float e1 = (hj - (s1 - bp)) + (vj - bp);
+            const float l1 = __uint_as_float(l[j]) + e1;
+            const float h2 = s1 + l1;
+            h[j] = __float_as_uint(h2);
+            l[j] = __float_as_uint(l1 - (h2 - s1));
+          }
+        }
+        if (!last) {
+          tmem_st32(t_hi + c0, h);
+          tmem_st32(t_lo + c0, l);
+        } else if (row_ok) {
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) {
             const int col = n0 + c0 + j;
-            if (col >= N2) break;
+            if (col >= N2) continue;
             const int n = col >> 1;
-            const double sc = ldexp(1.0, em + fB[(long long)p * N + n] - two_beta);
-            z64 t = mkc(((double)v[j] + (double)lv[j]) * sc, ((double)v[j + 1] + (double)lv[j + 1]) * sc);
+            const int sh = em + fBp[n] - two_beta;
+            z64 t = mkc(f32_scaled(h[j], sh) + f32_scaled(l[j], sh),
+                        f32_scaled(h[j + 1], sh) + f32_scaled(l[j + 1], sh));
             z64 o = unit_alpha ? t : alpha * t;
             if (use_beta) o = o + beta * crow[n];
             if (drow) o = o + (unit_gamma ? drow[n] : gamma * drow[n]);
@@ -454,12 +526,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       }
+      tmem_st_wait();
       tc_fence_before();
       mbar_arrive(&accempty[buf]);
     }
   }
   __syncthreads();
-  if (warp == 5) {
+  if (warp == 9) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
@@ -495,45 +568,53 @@ bool make_map(CUtensorMap* m, void* base, int L, int rows, long long zdim, int b
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// Every order d = s + t - 1 <= S is its own exact accumulator group; within a group each
-// (s, t) product is one item (A slice s, B slice t).
-Sched build_sched(int S, int maxt) {
+// Exact accumulator groups: for every K part and every order d = s + t - 1 <= S, one group
+// holding the products (s, t) of that order over that part of K.
+Sched build_sched(int S, int n_chunks, int n_parts) {
   Sched sc;
   std::memset(&sc, 0, sizeof(sc));
-  (void)maxt;
-  int n = 0;
-  for (int d = 1; d <= S; ++d)
-    for (int s = 1; s <= d && n < kMaxItems; ++s)
-      sc.it[n++] = Item{(int8_t)(d - 1), (int8_t)s, (int8_t)(d + 1 - s), (int8_t)1};
+  n_parts = std::max(1, std::min(n_parts, std::min(kMaxParts, n_chunks)));
+  for (int q = 0; q < n_parts; ++q) {
+    sc.part_lo[q] = (int)((long long)n_chunks * q / n_parts);
+    sc.part_hi[q] = (int)((long long)n_chunks * (q + 1) / n_parts);
+  }
+  int n = 0, g = 0;
+  for (int q = 0; q < n_parts; ++q)
+    for (int d = 1; d <= S; ++d, ++g)
+      for (int s = 1; s <= d && n < kMaxItems; ++s)
+        sc.it[n++] = Item{(int8_t)g, (int8_t)s, (int8_t)(d + 1 - s), (int8_t)q};
   sc.n_items = n;
-  sc.n_acc = S;
+  sc.n_acc = g;
   return sc;
 }
 
-template <int NT, int MAXT>
+template <int NT, int STAGES>
 cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S, int two_beta,
-                      const CUtensorMap& mA, const CUtensorMap& mB, const TcWs& ws, z64 alpha,
+                      int n_parts, const CUtensorMap& mA, const CUtensorMap& mB, const TcWs& ws,
+                      const int32_t* zA, int zmA, const int32_t* zB, int zmB, z64 alpha,
                       z64 beta, z64 gamma, BM<double> C, BMc<double> D, bool add_identity,
                       const int32_t* active) {
-  using CF = Cfg<NT, MAXT>;
+  using CF = Cfg<NT, STAGES>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NT, MAXT>,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NT, STAGES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, CF::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  Sched sc = build_sched(S, MAXT);
+  if ((long long)std::min(n_parts, kMaxParts) * S * (S + 1) / 2 > kMaxItems)
+    return cudaErrorInvalidValue;  // schedule longer than the kernel's item table
+  Sched sc = build_sched(S, L / kKC, n_parts);
   dim3 grid((N2 + NT - 1) / NT, (M + kBM - 1) / kBM, P);
   {
     const double alg = 8.0 * M * (N2 / 2) * (double)K * P;
-    const double hw = 2.0 * grid.y * kBM * (double)grid.x * NT * L * sc.n_items * P;
+    const double hw = 2.0 * grid.y * kBM * (double)grid.x * NT * L * (S * (S + 1) / 2) * P;
     prof_flops(PROF_TC_GEMM, alg, hw);
   }
   prof_begin(s, PROF_TC_GEMM);
-  k_tc_gemm<NT, MAXT><<<grid, kThreads, CF::kSmem, s>>>(
-      mA, mB, sc, M, N2, L, S, two_beta, ws.expA, ws.expB, ws.T64, alpha, beta, gamma, C, D,
-      add_identity ? 1 : 0, active, ws.err);
+  k_tc_gemm<NT, STAGES><<<grid, kThreads, CF::kSmem, s>>>(
+      mA, mB, sc, M, N2, S, two_beta, ws.expA, ws.expB, zA, zmA, zB, zmB, alpha, beta, gamma, C,
+      D, add_identity ? 1 : 0, active, ws.err);
   prof_end(s, PROF_TC_GEMM);
   count_launch();
   return cudaGetLastError();
@@ -541,19 +622,43 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
 
 }  // namespace
 
-void tc_plan(int K, int* beta, int* S) {
-  // Slice width beta and count S = ceil(48 / beta) such that every order group stays exact:
-  // the integer sum of group d over the 2K real terms is below 2K 2^(2 beta) (1 + (d-2)/4),
-  // which must not exceed 2^24 for d = S.
-  const double K2 = 2.0 * std::max(K, 1);
-  int b = 8;
-  for (; b > 1; --b) {
+// Kernel configuration (autotuner knob): index = 2 * stage_choice + part_choice with
+// stage_choice 0/1/2 = 4/6/7 pipeline stages and part_choice 0/1 = at most 4/8 K parts.
+std::atomic<int> g_cfg{2};
+constexpr int kNumCfg = 6;
+
+void tc_plan(int K, int* beta, int* S, int* parts, int max_parts) {
+  // Slices of beta bits, S = ceil(48 / beta), and the number of K parts such that every group
+  // of one order over one part sums to an integer below 2^24 and stays exact in FP32:
+  // 2 Kpart 2^(2 beta) (1 + (S - 2) / 4) <= 2^24.  The widest beta with at most 4 parts wins
+  // (fewest slice products), falling back to narrower digits for very long K.
+  const int nch = std::max(1, (2 * K + kKC - 1) / kKC);
+  for (int b = 8; b >= 2; --b) {
     const int s = std::min(kMaxS, (48 + b - 1) / b);
     const double grow = 1.0 + std::max(0, s - 2) / 4.0;
-    if (K2 * std::ldexp(1.0, 2 * b) * grow <= 16777216.0) break;
+    const double kmax = 16777216.0 / (std::ldexp(1.0, 2 * b) * grow);  // real terms per part
+    const int chunks_per_part = (int)std::floor(kmax / kKC);
+    if (chunks_per_part < 1) continue;
+    const int np = (nch + chunks_per_part - 1) / chunks_per_part;
+    if (np <= max_parts || b == 2) {
+      *beta = b;
+      *S = s;
+      *parts = std::min(np, kMaxParts);
+      return;
+    }
   }
-  *beta = b;
-  *S = std::min(kMaxS, (48 + b - 1) / b);
+  *beta = 2;
+  *S = kMaxS;
+  *parts = 1;
+}
+
+void tc_plan(int K, int* beta, int* S, int* parts) {
+  tc_plan(K, beta, S, parts, g_cfg.load() % 2 == 0 ? 4 : 8);
+}
+
+void tc_plan(int K, int* beta, int* S) {
+  int parts;
+  tc_plan(K, beta, S, &parts);
 }
 
 size_t tc_ws_bytes(int P, int M, int N, int K) {
@@ -564,8 +669,14 @@ size_t tc_ws_bytes(int P, int M, int N, int K) {
 }
 
 void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, TcWs& w) {
-  int beta, S;
-  tc_plan(K, &beta, &S);
+  // sized for the largest slice count over the K-part policies, so that a configuration
+  // change between sizing and use cannot overrun the workspace
+  int S = 0;
+  for (int mp : {4, 8}) {
+    int b2, s2, p2;
+    tc_plan(K, &b2, &s2, &p2, mp);
+    S = std::max(S, s2);
+  }
   const size_t L = (size_t)round_up(2 * K, kKC);
   auto take = [&](size_t bytes) -> void* {
     size_t a = (off + 1023) & ~size_t(1023);
@@ -576,14 +687,37 @@ void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, TcWs& w) {
   w.slicesB = take((size_t)P * S * 2 * N * L * 2);
   w.expA = static_cast<int32_t*>(take((size_t)P * M * 4));
   w.expB = static_cast<int32_t*>(take((size_t)P * N * 4));
-  w.T64 = static_cast<double*>(take((size_t)P * M * 2 * N * 8));
   w.err = static_cast<int32_t*>(take(256));
 }
 
 cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<double> A,
                     int opA, BMc<double> B, int opB, z64 beta, BM<double> C, z64 gamma,
-                    BMc<double> D, bool add_identity, const int32_t* active, const TcWs& ws) {
+                    BMc<double> D, bool add_identity, const int32_t* active, const TcWs& ws,
+                    int n_distinct) {
   if (P <= 0 || M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+  // Operands shared by all items (stride 0) or selected per item from n_distinct matrices are
+  // sliced once per distinct matrix; the kernel maps each item to its slice set.
+  auto plan_op = [&](BMc<double>& X, const int32_t*& z, int& mode, int& items) {
+    z = nullptr;
+    mode = 0;
+    items = P;
+    if (!X.idx && X.stride == 0) {
+      mode = 2;
+      items = 1;
+    } else if (X.idx && n_distinct > 0 && n_distinct <= P) {
+      mode = 1;
+      z = X.idx;
+      items = n_distinct;
+      X.idx = nullptr;
+    }
+  };
+  const int32_t *zA = nullptr, *zB = nullptr;
+  int zmA = 0, zmB = 0, PA = P, PB = P;
+  plan_op(A, zA, zmA, PA);
+  plan_op(B, zB, zmB, PB);
+  // with a shared operand the active mask cannot gate the slicing by item
+  const int32_t* actA = zmA == 0 ? active : nullptr;
+  const int32_t* actB = zmB == 0 ? active : nullptr;
   int bta, S;
   tc_plan(K, &bta, &S);
   const int L = round_up(2 * K, kKC);
@@ -591,34 +725,49 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
   __nv_bfloat16* sa = static_cast<__nv_bfloat16*>(ws.slicesA);
   __nv_bfloat16* sb = static_cast<__nv_bfloat16*>(ws.slicesB);
   prof_begin(s, PROF_SLICE);
-  k_slice_a<<<dim3((M + 7) / 8, P), 256, 0, s>>>(M, K, L, S, bta, A, opA, sa, ws.expA, active);
+  // a row of op(A) is a column of A in memory for op T/C; a column of op(B) is a column of B for
+  // op N
+  k_slice<false><<<dim3((M + 31) / 32, PA), 256, 0, s>>>(M, K, L, S, bta, A, opA, opA != OP_N,
+                                                         sa, ws.expA, actA);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_slice_b<<<dim3((N + 7) / 8, P), 256, 0, s>>>(K, N, L, S, bta, B, opB, sb, ws.expB, active);
+  k_slice<true><<<dim3((N + 31) / 32, PB), 256, 0, s>>>(N, K, L, S, bta, B, opB, opB == OP_N, sb,
+                                                        ws.expB, actB);
   prof_end(s, PROF_SLICE);
   count_launch(2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  // tile width: least padding of the 2N real columns, wider on ties
-  static const int widths[5] = {256, 224, 192, 160, 128};
-  int best = 128;
-  long long best_pad = -1;
-  for (int wdt : widths) {
-    long long pad = (long long)((N2 + wdt - 1) / wdt) * wdt;
-    if (best_pad < 0 || pad < best_pad) {
-      best_pad = pad;
-      best = wdt;
-    }
-  }
+  int parts;
+  tc_plan(K, &bta, &S, &parts);
   CUtensorMap mA, mB;
-  if (!make_map(&mA, sa, L, M, (long long)P * S, kBM)) return cudaErrorInvalidValue;
-  if (!make_map(&mB, sb, L, N2, (long long)P * S, best)) return cudaErrorInvalidValue;
-  switch (best) {
-    case 256: return launch_tc<256, 1>(s, P, M, N2, K, L, S, 2 * bta, mA, mB, ws, alpha, beta, gamma, C, D, add_identity, active);
-    case 224: return launch_tc<224, 1>(s, P, M, N2, K, L, S, 2 * bta, mA, mB, ws, alpha, beta, gamma, C, D, add_identity, active);
-    case 192: return launch_tc<192, 1>(s, P, M, N2, K, L, S, 2 * bta, mA, mB, ws, alpha, beta, gamma, C, D, add_identity, active);
-    case 160: return launch_tc<160, 1>(s, P, M, N2, K, L, S, 2 * bta, mA, mB, ws, alpha, beta, gamma, C, D, add_identity, active);
-    default: return launch_tc<128, 1>(s, P, M, N2, K, L, S, 2 * bta, mA, mB, ws, alpha, beta, gamma, C, D, add_identity, active);
+  if (!make_map(&mA, sa, L, M, (long long)PA * S, kBM)) return cudaErrorInvalidValue;
+  if (!make_map(&mB, sb, L, N2, (long long)PB * S, kNT)) return cudaErrorInvalidValue;
+  switch (g_cfg.load() / 2) {
+    case 0:
+      return launch_tc<kNT, 4>(s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB,
+                               zmB, alpha, beta, gamma, C, D, add_identity, active);
+    case 2:
+      return launch_tc<kNT, 7>(s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB,
+                               zmB, alpha, beta, gamma, C, D, add_identity, active);
+    default:
+      return launch_tc<kNT, 6>(s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB,
+                               zmB, alpha, beta, gamma, C, D, add_identity, active);
   }
 }
 
 }  // namespace negf
+
+using namespace negf;
+
+extern "C" {
+
+int32_t negf_tc_config_count(void) { return kNumCfg; }
+
+negf_status negf_tc_config_set(int32_t idx) {
+  if (idx < 0 || idx >= kNumCfg) return NEGF_ERR_ARG;
+  g_cfg.store(idx);
+  return NEGF_OK;
+}
+
+int32_t negf_tc_config_get(void) { return g_cfg.load(); }
+
+}  // extern "C"

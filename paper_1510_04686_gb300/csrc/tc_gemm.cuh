@@ -4,10 +4,11 @@
 //
 // Each operand row (A) / column (B) is scaled by a power of two and cut into S fixed-point
 // slices of beta bits stored as BF16 (exact).  Slice products are exact in BF16 x BF16 -> FP32
-// and, with beta chosen from K, every group of slice pairs of one order s + t - 1 sums to an
-// integer below 2^24 and is exact in its FP32 TMEM accumulator (the tensor core's accumulation
-// truncates, so inexact groups would lose bits linearly in K); the groups are added in FP64 in
-// the epilogue.  Products of order > S are dropped (below 2^-48 of the scale).  The complex product
+// and, with beta and a split of K into parts chosen from K, every group of slice pairs of one
+// order s + t - 1 over one part sums to an integer below 2^24 and is exact in its FP32 TMEM
+// accumulator (the tensor core's accumulation truncates, so inexact groups would lose bits
+// linearly in K); the groups are added into a TMEM-resident FP32-pair sum and converted to FP64
+// once in the epilogue.  Products of order > S are dropped (below 2^-48 of the scale).  The complex product
 // uses the real embedding  [Re A, Im A] x [[Re B, Im B], [-Im B, Re B]]  so that one MMA chain
 // produces interleaved (re, im) outputs.
 #pragma once
@@ -20,7 +21,6 @@ struct TcWs {
   void* slicesB;        // bf16 [P][S][2N][L]
   int32_t* expA;        // [P][M]
   int32_t* expB;        // [P][N]
-  double* T64;          // [P][M][2N] partial sums between accumulator groups
   int32_t* err;         // device error word (bounded waits that gave up)
 };
 
@@ -28,11 +28,16 @@ struct TcWs {
 size_t tc_ws_bytes(int P, int M, int N, int K);
 void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, TcWs& w);
 
-// Slices and exactness parameters used for a contraction length K (complex).
+// Slices and exactness parameters used for a contraction length K (complex): digit width beta,
+// slice count S and the number of K parts that are accumulated as separate exact groups.
 void tc_plan(int K, int* beta, int* S);
+void tc_plan(int K, int* beta, int* S, int* parts);
 
+// n_distinct: number of different matrices an indexed operand (idx != NULL) selects from
+// (0 = unknown: slice every item).
 cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<double> A,
                     int opA, BMc<double> B, int opB, z64 beta, BM<double> C, z64 gamma,
-                    BMc<double> D, bool add_identity, const int32_t* active, const TcWs& ws);
+                    BMc<double> D, bool add_identity, const int32_t* active, const TcWs& ws,
+                    int n_distinct = 0);
 
 }  // namespace negf

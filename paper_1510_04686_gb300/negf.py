@@ -49,7 +49,8 @@ EXPORTS = ("negf_default_options", "negf_abi_version", "negf_status_string",
            "negf_rgf_adjoint", "negf_integrate", "negf_zgemm_workspace_size",
            "negf_zgemm_batched", "negf_zinv_workspace_size", "negf_zinv_batched",
            "negf_profile_enable", "negf_profile_reset", "negf_profile_read", "negf_profile_flops",
-           "negf_launch_count", "negf_zinv_batched_noalloc")
+           "negf_launch_count", "negf_zinv_batched_noalloc", "negf_tc_config_count",
+           "negf_tc_config_set", "negf_tc_config_get")
 
 
 def library():
@@ -109,6 +110,12 @@ def library():
     lib.negf_launch_count.restype = ctypes.c_longlong
     lib.negf_zinv_batched_noalloc.argtypes = [c_int32, c_int32, P, P, P, P]
     lib.negf_zinv_batched_noalloc.restype = c_int32
+    lib.negf_tc_config_count.argtypes = []
+    lib.negf_tc_config_count.restype = c_int32
+    lib.negf_tc_config_set.argtypes = [c_int32]
+    lib.negf_tc_config_set.restype = c_int32
+    lib.negf_tc_config_get.argtypes = []
+    lib.negf_tc_config_get.restype = c_int32
     _LIB = lib
     return lib
 
@@ -406,3 +413,15 @@ class RGFFunction(torch.autograd.Function):
 def rgf(V, dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R=None, scat_L=None, e_idx=None):
     """Differentiable (density, current) of the points with respect to V."""
     return RGFFunction.apply(V, dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R, scat_L, e_idx)
+
+
+def tc_config(idx=None):
+    """Get (and with idx, set) the tensor-core GEMM kernel configuration."""
+    lib = library()
+    if idx is not None:
+        _check(lib.negf_tc_config_set(int(idx)), "negf_tc_config_set")
+    return int(lib.negf_tc_config_get())
+
+
+def tc_config_count():
+    return int(library().negf_tc_config_count())

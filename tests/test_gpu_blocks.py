@@ -107,3 +107,23 @@ def test_zinv_reports_singular():
     X, st = negf.zinv(M, precision=0)
     st = st.cpu().numpy()
     assert st[0] == 0 and (st[1] & 2)
+
+
+def test_zgemm_every_kernel_configuration():
+    """All tensor-core kernel configurations (pipeline depth, K-part policy) give the product to
+    the stated accuracy; the default is restored afterwards."""
+    rng = np.random.default_rng(21)
+    nb, n = 3, 400
+    A = _rand(rng, (nb, n, n))
+    B = _rand(rng, (nb, n, n))
+    ref = A @ B
+    tol = 1e-13 * _bound(A, B, "N", "N")
+    At, Bt = torch.as_tensor(A, device="cuda"), torch.as_tensor(B, device="cuda")
+    old = negf.tc_config()
+    try:
+        for c in range(negf.tc_config_count()):
+            negf.tc_config(c)
+            C = negf.zgemm(At, Bt, precision=1).cpu().numpy()
+            assert np.all(np.abs(C - ref) <= tol), c
+    finally:
+        negf.tc_config(old)
