@@ -31,6 +31,10 @@ WORK = dict(N=70, b=400, n_E=512, n_k=8, ge_frac=0.1, eta=1e-6, seed=1001,
             name="ballistic RGF, N=70 slabs x 400x400 blocks, alloy p(Ge)=0.1, 512 E x 8 k")
 METRIC = "RGF energy-points/s (leads + forward/backward sweeps + observables + FP64 quadrature)"
 PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0)
+# DRAM bytes (read + write) of k_tc_gemm per 400 x 400 x 400 complex item, from the ncu capture
+# summarised in profiles/tc_gemm_b400_x64.md (64 items: 920.6 MB read + 152.0 MB written).
+# Valid for the kernel version profiled there; the traffic of a launch scales with its items.
+TC_DRAM_BYTES_PER_ITEM_B400 = (920.555008e6 + 152.032512e6) / 64
 
 
 def parse():
@@ -232,11 +236,13 @@ def main():
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("bench_timed")  # lets a profiler select the timed launches
         ev0.record()
         for s in range(args.warmup, total_steps):
             step(s)
         ev1.record()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = negf.launch_count() - l0
     negf.profile(False)
     ms = ev0.elapsed_time(ev1)
@@ -265,7 +271,9 @@ def main():
         "issued_frac": ((hw / (tc_ms / 1e3)) / 1e12 / peak_bf16) if tc_ms > 0 else None,
         "share_of_step": tc_ms / ms if ms > 0 else None,
         "slicing_share_of_step": sl_ms / ms if ms > 0 else None,
-        "traffic": None,
+        "traffic": (TC_DRAM_BYTES_PER_ITEM_B400 * (alg / max(n_launch, 1)) / (8.0 * WORK["b"] ** 3)
+                    if WORK["b"] == 400 and n_launch else None),
+        "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
     }
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
