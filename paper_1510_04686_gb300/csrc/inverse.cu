@@ -79,7 +79,8 @@ __device__ __forceinline__ cx<R> pivot_recip(cx<R> a, int32_t* st) {
 }
 
 // One Gauss-Jordan step on column jj of an (rows x w) shared-memory array P (row stride w)
-// whose pivot row is `j`.  Uses f[rows] scratch.
+// whose pivot row is `j`.  Uses f[rows] scratch.  Thread t works on column t % w of rows
+// t / w, t / w + blockDim / w, ... (no index division in the loops).
 template <typename R>
 __device__ void gj_step(cx<R>* P, int rows, int w, int j, int jj, cx<R>* f, int32_t* st) {
   for (int r = threadIdx.x; r < rows; r += blockDim.x) f[r] = P[(long long)r * w + jj];
@@ -90,19 +91,41 @@ __device__ void gj_step(cx<R>* P, int rows, int w, int j, int jj, cx<R>* f, int3
     e = (c == jj) ? d : e * d;
   }
   __syncthreads();
-  const long long tot = (long long)rows * w;
-  for (long long e = threadIdx.x; e < tot; e += blockDim.x) {
-    int r = (int)(e / w), c = (int)(e % w);
-    if (r == j) continue;
-    cx<R> fr = f[r];
-    if (c == jj) {
-      P[e] = mkc<R>(R(0), R(0)) - fr * d;
-    } else {
-      cx<R> v = P[e];
-      cx<R> pj = P[(long long)j * w + c];
-      v.re = v.re - (fr.re * pj.re - fr.im * pj.im);
-      v.im = v.im - (fr.re * pj.im + fr.im * pj.re);
-      P[e] = v;
+  if (w <= (int)blockDim.x) {
+    const int c = threadIdx.x % w;
+    const int r0 = threadIdx.x / w, rstep = blockDim.x / w;
+    if (r0 < rstep) {
+      const cx<R> pj = P[(long long)j * w + c];
+      for (int r = r0; r < rows; r += rstep) {
+        if (r == j) continue;
+        const cx<R> fr = f[r];
+        cx<R>* e = P + (long long)r * w + c;
+        if (c == jj) {
+          *e = mkc<R>(R(0), R(0)) - fr * d;
+        } else {
+          cx<R> v = *e;
+          v.re = v.re - (fr.re * pj.re - fr.im * pj.im);
+          v.im = v.im - (fr.re * pj.im + fr.im * pj.re);
+          *e = v;
+        }
+      }
+    }
+  } else {
+    for (int r = 0; r < rows; ++r) {
+      if (r == j) continue;
+      const cx<R> fr = f[r];
+      for (int c = threadIdx.x; c < w; c += blockDim.x) {
+        cx<R>* e = P + (long long)r * w + c;
+        if (c == jj) {
+          *e = mkc<R>(R(0), R(0)) - fr * d;
+        } else {
+          const cx<R> pj = P[(long long)j * w + c];
+          cx<R> v = *e;
+          v.re = v.re - (fr.re * pj.re - fr.im * pj.im);
+          v.im = v.im - (fr.re * pj.im + fr.im * pj.re);
+          *e = v;
+        }
+      }
     }
   }
   __syncthreads();
@@ -173,9 +196,9 @@ __global__ void __launch_bounds__(kThreads) k_gj_panel(int n, int k0, int w, int
   cx<R>* a = bat(Am, p);
   const long long ld = Am.ld;
   int32_t* pv = piv + (long long)p * n;
-  for (long long e = threadIdx.x; e < (long long)n * w; e += blockDim.x) {
-    int r = (int)(e / w), c = (int)(e % w);
-    P[e] = a[r * ld + k0 + c];
+  for (int r = threadIdx.x / w; r < n; r += blockDim.x / w) {
+    const int c = threadIdx.x % w;
+    if (threadIdx.x / w < (int)blockDim.x / w) P[(long long)r * w + c] = a[r * ld + k0 + c];
   }
   __syncthreads();
   for (int jj = 0; jj < w; ++jj) {
@@ -201,21 +224,25 @@ __global__ void __launch_bounds__(kThreads) k_gj_panel(int n, int k0, int w, int
   }
   // T = pivot rows (panel columns zeroed); those rows of A are cleared outside the panel
   cx<R>* Tp = T + (long long)p * nb * n;
-  for (long long e = threadIdx.x; e < (long long)w * n; e += blockDim.x) {
-    int jj = (int)(e / n), c = (int)(e % n);
-    cx<R>* ae = a + (long long)(k0 + jj) * ld + c;
-    if (c >= k0 && c < k0 + w) {
-      Tp[(long long)jj * n + c] = mkc<R>(R(0), R(0));
-    } else {
-      Tp[(long long)jj * n + c] = *ae;
-      *ae = mkc<R>(R(0), R(0));
+  for (int jj = 0; jj < w; ++jj) {
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      cx<R>* ae = a + (long long)(k0 + jj) * ld + c;
+      if (c >= k0 && c < k0 + w) {
+        Tp[(long long)jj * n + c] = mkc<R>(R(0), R(0));
+      } else {
+        Tp[(long long)jj * n + c] = *ae;
+        *ae = mkc<R>(R(0), R(0));
+      }
     }
   }
   cx<R>* Up = U + (long long)p * n * nb;
-  for (long long e = threadIdx.x; e < (long long)n * w; e += blockDim.x) {
-    int r = (int)(e / w), c = (int)(e % w);
-    a[r * ld + k0 + c] = P[e];
-    Up[(long long)r * nb + c] = P[e];
+  for (int r = threadIdx.x / w; r < n; r += blockDim.x / w) {
+    const int c = threadIdx.x % w;
+    if (threadIdx.x / w < (int)blockDim.x / w) {
+      const cx<R> v = P[(long long)r * w + c];
+      a[r * ld + k0 + c] = v;
+      Up[(long long)r * nb + c] = v;
+    }
   }
 }
 

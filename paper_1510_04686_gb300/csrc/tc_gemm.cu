@@ -214,7 +214,7 @@ __device__ __forceinline__ void cut(double x, int e, int S, int beta, float* out
     const int shs = 62 - beta * (s + 1);
     const long long q = (R + (1ll << (shs - 1))) >> shs;
     R -= q << shs;
-    const float v = (float)q * scale;
+    const float v = (float)(int)q * scale;  // |q| <= 2^8: exact through a 32-bit integer
     out[s] = neg ? -v : v;
     scale *= step;
   }
