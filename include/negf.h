@@ -248,9 +248,9 @@ negf_status negf_zinv_batched_noalloc(int32_t n_batch, int32_t n, double* M, dou
 
 /* ---- tensor-core GEMM configuration (autotuning) ----------------------------------------
  * The mixed-precision GEMM has negf_tc_config_count() kernel configurations, differing only in
- * speed: configuration c uses (4, 6, 7)[c / 2] pipeline stages and splits K into at most
+ * speed: configuration c uses (4, 5, 6)[c / 2] pipeline stages and splits K into at most
  * (4, 8)[c % 2] exactly accumulated parts (more parts allow wider slices and fewer slice
- * products).  negf_tc_config_set selects one process-wide (default 2); results agree to the
+ * products).  negf_tc_config_set selects one process-wide (default 4); results agree to the
  * GEMM's rounding.  The package's autotuner times them per block size and stores the choice. */
 int32_t negf_tc_config_count(void);
 negf_status negf_tc_config_set(int32_t idx);

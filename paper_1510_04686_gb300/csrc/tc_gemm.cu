@@ -326,7 +326,9 @@ struct Cfg {
   static constexpr int kATile = kBM * kKC * 2;                // 16 KB
   static constexpr int kBTile = NT * kKC * 2;
   static constexpr int kStage = kATile + kBTile;
-  static constexpr int kSmem = kStages * kStage + 1024 + 256;  // + alignment + barriers
+  static constexpr int kStagingPerWarp = 32 * 8 * 16;         // 32 rows x 8 complex outputs
+  static constexpr int kStaging = kEpiWarps * kStagingPerWarp;
+  static constexpr int kSmem = kStages * kStage + kStaging + 1024 + 256;  // + align + barriers
 };
 
 template <int NT, int STAGES>
@@ -346,7 +348,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * CF::kStage);
+  z64* staging = reinterpret_cast<z64*>(smem + kStages * CF::kStage);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * CF::kStage + CF::kStaging);
   uint64_t* empty = full + kStages;
   uint64_t* accfull = empty + kStages;
   uint64_t* accempty = accfull + 2;
@@ -466,8 +469,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int em = row_ok ? eA[(long long)zA * M + m] : 0;
     const int N = N2 >> 1;
     const int32_t* fBp = fB + (long long)zB * N;
-    z64* crow = row_ok ? bat(C, p) + (long long)m * C.ld : nullptr;
-    const z64* drow = (row_ok && D.p) ? bat(D, p) + (long long)m * D.ld : nullptr;
     const bool use_beta = (beta.re != 0.0 || beta.im != 0.0);
     const bool unit_alpha = (alpha.re == 1.0 && alpha.im == 0.0);
     const bool unit_gamma = (gamma.re == 1.0 && gamma.im == 0.0);
@@ -509,20 +510,40 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!last) {
           tmem_st32(t_hi + c0, h);
           tmem_st32(t_lo + c0, l);
-        } else if (row_ok) {
+        } else {
+          // Final value of this row's 16 complex outputs, written through a per-warp staging
+          // tile so that C, D and the stores are accessed as contiguous 128-byte row segments.
+          z64* stg = staging + warp * (32 * 8);
 #pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            const int col = n0 + c0 + j;
-            if (col >= N2) continue;
-            const int n = col >> 1;
-            const int sh = em + fBp[n] - two_beta;
-            z64 t = mkc(f32_scaled(h[j], sh) + f32_scaled(l[j], sh),
-                        f32_scaled(h[j + 1], sh) + f32_scaled(l[j + 1], sh));
-            z64 o = unit_alpha ? t : alpha * t;
-            if (use_beta) o = o + beta * crow[n];
-            if (drow) o = o + (unit_gamma ? drow[n] : gamma * drow[n]);
-            if (add_identity && n == m) o.re += 1.0;
-            crow[n] = o;
+          for (int half8 = 0; half8 < 2; ++half8) {
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              const int j = 16 * half8 + 2 * jj;
+              const int n = (n0 + c0 + j) >> 1;
+              const int sh = em + (n < N ? fBp[n] : 0) - two_beta;
+              stg[lane * 8 + jj] = mkc(f32_scaled(h[j], sh) + f32_scaled(l[j], sh),
+                                       f32_scaled(h[j + 1], sh) + f32_scaled(l[j + 1], sh));
+            }
+            __syncwarp();
+            const int nb0 = (n0 + c0) / 2 + 8 * half8;  // first complex column of this piece
+#pragma unroll
+            for (int it = 0; it < 8; ++it) {
+              const int rl = it * 4 + (lane >> 3), cj = lane & 7;
+              const int mr = m0 + q * 32 + rl, n = nb0 + cj;
+              if (mr < M && n < N) {
+                const z64 t = stg[rl * 8 + cj];
+                z64 o = unit_alpha ? t : alpha * t;
+                z64* cp = bat(C, p) + (long long)mr * C.ld + n;
+                if (use_beta) o = o + beta * (*cp);
+                if (D.p) {
+                  const z64 dv = bat(D, p)[(long long)mr * D.ld + n];
+                  o = o + (unit_gamma ? dv : gamma * dv);
+                }
+                if (add_identity && n == mr) o.re += 1.0;
+                *cp = o;
+              }
+            }
+            __syncwarp();
           }
         }
       }
@@ -623,8 +644,8 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
 }  // namespace
 
 // Kernel configuration (autotuner knob): index = 2 * stage_choice + part_choice with
-// stage_choice 0/1/2 = 4/6/7 pipeline stages and part_choice 0/1 = at most 4/8 K parts.
-std::atomic<int> g_cfg{2};
+// stage_choice 0/1/2 = 4/5/6 pipeline stages and part_choice 0/1 = at most 4/8 K parts.
+std::atomic<int> g_cfg{4};
 constexpr int kNumCfg = 6;
 
 void tc_plan(int K, int* beta, int* S, int* parts, int max_parts) {
@@ -745,8 +766,8 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
     case 0:
       return launch_tc<kNT, 4>(s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB,
                                zmB, alpha, beta, gamma, C, D, add_identity, active);
-    case 2:
-      return launch_tc<kNT, 7>(s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB,
+    case 1:
+      return launch_tc<kNT, 5>(s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB,
                                zmB, alpha, beta, gamma, C, D, add_identity, active);
     default:
       return launch_tc<kNT, 6>(s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB,
