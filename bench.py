@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--points-per-step", type=int, default=64)
+    ap.add_argument("--points-per-step", type=int, default=128)
     ap.add_argument("--cpu-points", type=int, default=2)
     ap.add_argument("--fp64-points", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true",

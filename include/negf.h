@@ -97,10 +97,16 @@ typedef struct {
   int32_t refine_steps;  /* mixed precision: Newton-Schulz steps X <- X + X (I - M X) after
                             each block inverse (default 2)                                  */
   int32_t chunk;         /* points solved concurrently (0 = library default)                */
+  int32_t sr_host_check; /* decimation: read the count of unconverged points back every this
+                            many steps (after 8) and stop early; 0 = never read back: always run
+                            sr_max_iter steps with converged points masked on the device, so the
+                            call makes no host synchronisation (CUDA-graph capturable).  Default 4 */
+  int32_t reserved;
 } negf_options;
 
 /* Fill `opt` with the defaults (eta 1e-6 in leads and device, mu_L = +0.1, mu_R = -0.1,
- * kT = 0.025852, sr_tol = 1e-13, sr_max_iter = 100, FP64, refine_steps = 2, chunk = 0). */
+ * kT = 0.025852, sr_tol = 1e-13, sr_max_iter = 100, FP64, refine_steps = 2, chunk = 0,
+ * sr_host_check = 4). */
 void negf_default_options(negf_options* opt);
 
 int32_t negf_abi_version(void);

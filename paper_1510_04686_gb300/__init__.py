@@ -20,6 +20,7 @@ from .negf import (  # noqa: F401
     launch_count,
     PROF_TC_GEMM,
     RGFFunction,
+    GraphSolve,
     tc_config,
     tc_config_count,
     rgf,

@@ -47,6 +47,7 @@ bool valid_opt(const negf_options* o) {
   if (!(o->sr_tol > 0.0) || o->sr_max_iter < 1 || o->sr_max_iter > 100000) return false;
   if (o->precision != NEGF_PREC_FP64 && o->precision != NEGF_PREC_MIXED) return false;
   if (o->refine_steps < 0 || o->refine_steps > 8 || o->chunk < 0) return false;
+  if (o->sr_host_check < 0) return false;
   return true;
 }
 
@@ -195,7 +196,8 @@ negf_status lead_chunk_run(const negf_device* dev, int P, const double* E, const
     CK(cudaMemsetAsync(w.n_active, 0, sizeof(int32_t), s));
     CK(launch_sr_check(s, Q, b, it, opt->sr_tol, cst(flat(al, bb, b)), cst(flat(be, bb, b)),
                        w.scale, w.active, w.iters, w.n_active));
-    if (it >= 8 && (it % 4 == 0 || it == opt->sr_max_iter)) {
+    const int chk = opt->sr_host_check;
+    if (chk > 0 && it >= 8 && (it % chk == 0 || it == opt->sr_max_iter)) {
       CK(cudaMemcpyAsync(&h_active, w.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (h_active == 0) break;
@@ -386,6 +388,8 @@ void negf_default_options(negf_options* o) {
   o->precision = NEGF_PREC_FP64;
   o->refine_steps = 2;
   o->chunk = 0;
+  o->sr_host_check = 4;
+  o->reserved = 0;
 }
 
 int32_t negf_abi_version(void) { return NEGF_ABI_VERSION; }

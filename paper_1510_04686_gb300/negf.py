@@ -40,7 +40,7 @@ class _Opt(ctypes.Structure):
     _fields_ = [("eta_lead", c_double), ("eta_device", c_double), ("mu_L", c_double),
                 ("mu_R", c_double), ("kT", c_double), ("sr_tol", c_double),
                 ("sr_max_iter", c_int32), ("precision", c_int32), ("refine_steps", c_int32),
-                ("chunk", c_int32)]
+                ("chunk", c_int32), ("sr_host_check", c_int32), ("reserved", c_int32)]
 
 
 _LIB = None
@@ -425,3 +425,39 @@ def tc_config(idx=None):
 
 def tc_config_count():
     return int(library().negf_tc_config_count())
+
+
+class GraphSolve:
+    """A lead + RGF solve of fixed points captured once in a CUDA graph and replayed.
+
+    The decimation runs a fixed sr_max_iter steps with converged points masked on the device
+    (sr_host_check = 0), so the captured sequence has no host synchronisation.  Inputs are the
+    tensors given here; change their contents in place and call replay() to solve again (for
+    example once per Born iteration with updated scattering self-energies).
+    """
+
+    def __init__(self, dev: Device, E, sys_idx, opt: _Opt, sr_steps: int = 40, V=None,
+                 scat_R=None, scat_L=None, e_idx=None, diag=False):
+        o = _Opt()
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(opt), ctypes.sizeof(_Opt))
+        o.sr_host_check = 0
+        o.sr_max_iter = sr_steps
+        self.opt = o
+        args = (dev, E, sys_idx)
+        kw = dict(V=V, scat_R=scat_R, scat_L=scat_L, e_idx=e_idx, diag=diag)
+        # warm-up outside capture: workspace allocation, kernel attributes, tensor-map encoder
+        lead = lead_selfenergy(*args, o)
+        rgf_solve(*args, lead["sigma_R"], lead["sigma_L"], o, **kw)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(self.graph, stream=s):
+                self.lead = lead_selfenergy(*args, o)
+                self.out = rgf_solve(*args, self.lead["sigma_R"], self.lead["sigma_L"], o, **kw)
+        torch.cuda.current_stream().wait_stream(s)
+
+    def replay(self):
+        self.graph.replay()
+        return self.out

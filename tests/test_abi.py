@@ -104,3 +104,11 @@ def test_binding_refuses_cpu_tensors():
     import torch
     with pytest.raises(TypeError):
         negf.Device(torch.zeros((1, 2, 3, 3), dtype=torch.complex128), None)
+
+
+def test_options_struct_layout():
+    # six doubles and six 32-bit integers, as in include/negf.h
+    assert ctypes.sizeof(B._Opt) == 6 * 8 + 6 * 4
+    assert ctypes.sizeof(B._Dev) == 4 * 4 + 2 * 8
+    o = negf.options()
+    assert o.sr_host_check == 4
