@@ -21,6 +21,7 @@ from .negf import (  # noqa: F401
     PROF_TC_GEMM,
     RGFFunction,
     GraphSolve,
+    solve_ragged,
     tc_config,
     tc_config_count,
     rgf,

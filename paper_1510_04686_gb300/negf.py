@@ -175,7 +175,8 @@ _WS = {}
 
 
 def _workspace(nbytes, device):
-    key = (str(device),)
+    # one buffer per (device, stream): calls on different streams may run concurrently
+    key = (str(device), torch.cuda.current_stream(device).cuda_stream)
     buf = _WS.get(key)
     if buf is None or buf.numel() < nbytes:
         _WS.pop(key, None)
@@ -461,3 +462,42 @@ class GraphSolve:
     def replay(self):
         self.graph.replay()
         return self.out
+
+
+def solve_ragged(systems, opt: _Opt, outputs=("density", "current", "transmission"),
+                 concurrent=True):
+    """Solve many systems of different block sizes: ``systems`` is a list of
+    (H_diag [N,b,b], H_up [N-1,b,b], E [n]) complex128 / float64 CUDA tensors.
+
+    Systems with the same (N, b) are stacked into one device (one batched lead + sweep chain per
+    group, points of every system of the group in one call); groups run on separate CUDA streams
+    so that small and large block sizes overlap.  Returns one result dict per system."""
+    groups = {}
+    for i, (Hd, Hu, E) in enumerate(systems):
+        groups.setdefault((int(Hd.shape[0]), int(Hd.shape[1])), []).append(i)
+    results = [None] * len(systems)
+    cur = torch.cuda.current_stream()
+    streams = []
+    for (N, b), idx in sorted(groups.items(), key=lambda kv: -kv[0][1]):
+        st = torch.cuda.Stream() if concurrent else cur
+        st.wait_stream(cur)
+        streams.append(st)
+        with torch.cuda.stream(st):
+            Hd = torch.stack([systems[i][0] for i in idx])
+            Hu = torch.stack([systems[i][1] for i in idx]) if N > 1 else None
+            dev = Device(Hd, Hu)
+            E = torch.cat([systems[i][2] for i in idx])
+            sys_idx = torch.cat([torch.full((systems[i][2].numel(),), j, dtype=torch.int32,
+                                            device=E.device) for j, i in enumerate(idx)])
+            lead = lead_selfenergy(dev, E, sys_idx, opt)
+            out = rgf_solve(dev, E, sys_idx, lead["sigma_R"], lead["sigma_L"], opt,
+                            outputs=outputs)
+            off = 0
+            for i in idx:
+                n = systems[i][2].numel()
+                results[i] = {k: (v[off:off + n] if isinstance(v, torch.Tensor) else v)
+                              for k, v in out.items()}
+                off += n
+    for st in streams:
+        cur.wait_stream(st)
+    return results
