@@ -49,6 +49,13 @@ def parse():
     ap.add_argument("--fp64-points", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU-oracle, FP64-GPU and end-to-end side measurements")
+    ap.add_argument("--workload", default="rgf", choices=["rgf", "scba", "adjoint", "ragged"],
+                    help="rgf: the throughput line above; scba / adjoint / ragged: side "
+                         "measurements of the Born loop (N=70, b=600), the adjoint sweep "
+                         "(b=3430) and ragged block sizes (b=200..800)")
+    ap.add_argument("--scba-energies", type=int, default=128)
+    ap.add_argument("--adj-slabs", type=int, default=20)
+    ap.add_argument("--ragged-points", type=int, default=16)
     return ap.parse_args()
 
 
@@ -169,10 +176,107 @@ def _blas_threads():
     return os.cpu_count()
 
 
+def _timed(torch, fn, warmup, steps):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def run_side(args):
+    """Side measurements for the Born loop, the adjoint sweep and ragged block sizes."""
+    import torch
+    import paper_1510_04686_gb300 as negf
+    from workloads import make_device, config_workload
+    torch.cuda.set_device(0)
+    negf._build.build()
+    dvc = torch.device("cuda", 0)
+    line = {"impl": "ours", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "data": "synthetic", "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None}
+    if args.workload == "scba":
+        w = config_workload(3, n_E=args.scba_energies)
+        dev, E, prm = w["device"], w["E"], w["params"]
+        N, b, nE = dev.N, dev.b, E.size
+        D = negf.Device(torch.as_tensor(dev.D[None], device=dvc), torch.as_tensor(dev.T[None], device=dvc))
+        Et = torch.as_tensor(E, device=dvc)
+        st = torch.zeros(nE, dtype=torch.int32, device=dvc)
+        opt = negf.options(precision=negf.PREC_MIXED, chunk=min(nE, 128))
+        lead = negf.lead_selfenergy(D, Et, st, opt)
+        sR = torch.zeros((nE, N * b), dtype=torch.complex128, device=dvc)
+        sL = torch.zeros_like(sR)
+        wk = torch.ones(1, dtype=torch.float64, device=dvc)
+        n0 = 1.0 / (np.exp(prm["hw"] / prm["kT"]) - 1.0)
+        deltas = []
+
+        def born():
+            out = negf.rgf_solve(D, Et, st, lead["sigma_R"], lead["sigma_L"], opt, scat_R=sR,
+                                 scat_L=sL, diag=True, outputs=("density", "current"))
+            d = negf.scba_step(out["diagGR"].reshape(1, nE, N * b), out["diagGL"].reshape(1, nE, N * b),
+                               wk, sR, sL, prm["D_ac"], prm["D_op"],
+                               int(round(prm["hw"] / prm["dE"])), n0)
+            deltas.append(d)
+            return out
+        ms, _ = _timed(torch, born, args.warmup, args.steps)
+        line.update(metric="SCBA point-iterations/s (RGF with phonon self-energies + Born update)",
+                    value=nE * args.steps / (ms / 1e3), unit="point-iterations/s",
+                    ms_per_step=ms / args.steps, dtype="bf16-slices->fp32 (fp64 storage)",
+                    config={"workload": f"SCBA N=70 b=600, energies 0..{nE - 1} of the 5 meV grid",
+                            "D_ac": 0.01, "D_op": 0.01, "hw_steps": 12,
+                            "last_delta": float(deltas[-1].item())})
+    elif args.workload == "adjoint":
+        w = config_workload(4, N=args.adj_slabs, n_E=1)
+        dev, V = w["device"], w["V"]
+        N, b = dev.N, dev.b
+        rng = np.random.default_rng(4)
+        D = negf.Device(torch.as_tensor(dev.D[None], device=dvc), torch.as_tensor(dev.T[None], device=dvc))
+        Et = torch.as_tensor(np.array([0.1]), device=dvc)
+        st = torch.zeros(1, dtype=torch.int32, device=dvc)
+        opt = negf.options(precision=negf.PREC_MIXED, chunk=1)
+        lead = negf.lead_selfenergy(D, Et, st, opt)
+        Vt = torch.as_tensor(V, device=dvc)
+        c = torch.as_tensor(rng.normal(size=(1, N * b)), device=dvc)
+        d = torch.as_tensor(rng.normal(size=(1, N - 1)), device=dvc)
+
+        def adj():
+            return negf.rgf_adjoint(D, Et, st, lead["sigma_R"], lead["sigma_L"], opt,
+                                    density_bar=c, current_bar=d, V=Vt)
+        ms, _ = _timed(torch, adj, args.warmup, args.steps)
+        line.update(metric="adjoint points/s (forward sweep kept + reverse sweep, dL/dV)",
+                    value=args.steps / (ms / 1e3), unit="points/s", ms_per_step=ms / args.steps,
+                    dtype="bf16-slices->fp32 (fp64 storage)",
+                    config={"workload": f"adjoint, N={N} slabs x 3430 orbitals (343 atoms x 10),"
+                                        " V ~ U(-0.3, 0.3) eV per atom, 1 point"})
+    else:
+        N, npts = 70, args.ragged_points
+        systems = []
+        for i, b in enumerate((200, 300, 400, 500, 600, 700, 800)):
+            dv = make_device(N, b, 2000 + i, ge_frac=0.1)
+            systems.append((torch.as_tensor(dv.D, device=dvc), torch.as_tensor(dv.T, device=dvc),
+                            torch.as_tensor(np.linspace(-2.5, 2.5, npts), device=dvc)))
+        opt = negf.options(precision=negf.PREC_MIXED)
+        ms, _ = _timed(torch, lambda: negf.solve_ragged(systems, opt), args.warmup, args.steps)
+        line.update(metric="RGF energy-points/s over ragged block sizes", unit="points/s",
+                    value=7 * npts * args.steps / (ms / 1e3), ms_per_step=ms / args.steps,
+                    dtype="bf16-slices->fp32 (fp64 storage)",
+                    config={"workload": f"7 alloy samples, b = 200..800, N = 70, {npts} E each",
+                            "grouping": "one batched chain per block size, concurrent streams"})
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload != "rgf":
+        run_side(args)
         return
     import torch
     import paper_1510_04686_gb300 as negf

@@ -464,6 +464,9 @@ class GraphSolve:
         return self.out
 
 
+_RAGGED_STREAMS = {}
+
+
 def solve_ragged(systems, opt: _Opt, outputs=("density", "current", "transmission"),
                  concurrent=True):
     """Solve many systems of different block sizes: ``systems`` is a list of
@@ -477,9 +480,16 @@ def solve_ragged(systems, opt: _Opt, outputs=("density", "current", "transmissio
         groups.setdefault((int(Hd.shape[0]), int(Hd.shape[1])), []).append(i)
     results = [None] * len(systems)
     cur = torch.cuda.current_stream()
+    # the side streams are kept across calls: each owns a cached workspace
+    pool = _RAGGED_STREAMS.setdefault(str(cur.device), [])
     streams = []
-    for (N, b), idx in sorted(groups.items(), key=lambda kv: -kv[0][1]):
-        st = torch.cuda.Stream() if concurrent else cur
+    for g, ((N, b), idx) in enumerate(sorted(groups.items(), key=lambda kv: -kv[0][1])):
+        if concurrent:
+            while len(pool) <= g:
+                pool.append(torch.cuda.Stream(device=cur.device))
+            st = pool[g]
+        else:
+            st = cur
         st.wait_stream(cur)
         streams.append(st)
         with torch.cuda.stream(st):

@@ -122,3 +122,37 @@ def test_autograd_function_uses_the_adjoint():
         (torch.as_tensor(d, device="cuda") * cur).sum()
     loss.backward()
     assert np.abs(Vt.grad.cpu().numpy() - g_ref).max() <= 1e-12 * np.abs(g_ref).max()
+
+
+def test_adjoint_finite_differences_on_16_atoms():
+    """Reduced copy of the Newton-Poisson workload (N = 10 slabs x 343 orbitals, potential per
+    atom of 10 orbitals): dL/dV_atom from the adjoint against central differences of the FP64
+    GPU solve for 16 atoms, delta = 1e-4 eV."""
+    from workloads import random_potential
+    N, b = 10, 343
+    dev = make_device(N, b, 4004)
+    rng = np.random.default_rng(4)
+    E = np.array([-0.45, 0.12])
+    V = random_potential(N, b, 4504, 0.3)
+    c = rng.normal(size=(len(E), N * b))
+    d = rng.normal(size=(len(E), N - 1))
+    opt = negf.options()
+    g, (D, Et, st, lead, kw) = _gpu_grad(dev, E, V, c, d, opt)
+
+    def loss(Vx):
+        out = negf.rgf_solve(D, Et, st, lead["sigma_R"], lead["sigma_L"], opt,
+                             V=torch.as_tensor(Vx, device="cuda"))
+        return float((c * out["density"].cpu().numpy()).sum()
+                     + (d * out["current"].cpu().numpy()).sum())
+
+    h = 1e-4
+    atoms = [(i, a) for i in range(0, N, 2) for a in (0, 11, 33)][:16]
+    for (i, a) in atoms:
+        sl = slice(10 * a, min(10 * a + 10, b))
+        Vp = V.copy()
+        Vm = V.copy()
+        Vp[i, sl] += h
+        Vm[i, sl] -= h
+        fd = (loss(Vp) - loss(Vm)) / (2 * h)
+        ga = g[i, sl].sum()
+        assert abs(fd - ga) <= 1e-5 * max(abs(ga), 1e-3 * np.abs(g).max()), (i, a, fd, ga)
