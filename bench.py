@@ -32,9 +32,9 @@ WORK = dict(N=70, b=400, n_E=512, n_k=8, ge_frac=0.1, eta=1e-6, seed=1001,
 METRIC = "RGF energy-points/s (leads + forward/backward sweeps + observables + FP64 quadrature)"
 PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0)
 # DRAM bytes (read + write) of k_tc_gemm per 400 x 400 x 400 complex item, from the ncu capture
-# summarised in profiles/tc_gemm_b400_x64.md (64 items: 920.6 MB read + 152.0 MB written).
-# Valid for the kernel version profiled there; the traffic of a launch scales with its items.
-TC_DRAM_BYTES_PER_ITEM_B400 = (920.555008e6 + 152.032512e6) / 64
+# summarised in profiles/tc_gemm_b400_x64.md; None while the kernel has changed since that
+# capture.  The traffic of a launch scales with its items.
+TC_DRAM_BYTES_PER_ITEM_B400 = None
 
 
 def parse():
@@ -301,6 +301,11 @@ def main():
     device = negf.Device(Hd_t, Hu_t)
     prec = negf.PREC_MIXED if args.precision == "mixed" else negf.PREC_FP64
     P = args.points_per_step
+    tuned = None
+    if prec == negf.PREC_MIXED:
+        # pick the tensor-core GEMM configuration for this block size and batch (untimed)
+        from paper_1510_04686_gb300 import autotune
+        tuned = autotune.tune_tc(WORK["b"], P)["config"]
     opt = negf.options(precision=prec, chunk=P)
     n_tot = WORK["n_E"] * WORK["n_k"]
     total_steps = args.warmup + args.steps
@@ -357,6 +362,7 @@ def main():
         dist.barrier()
     n_launch, tc_ms, alg, hw = negf.profile_read(negf.PROF_TC_GEMM)
     sl_n, sl_ms, _, _ = negf.profile_read(negf.PROF_SLICE)
+    inv_n, inv_ms, _, _ = negf.profile_read(negf.PROF_INV)
     points = args.steps * P * world
     value = points / (ms / 1e3)
 
@@ -375,8 +381,9 @@ def main():
         "issued_frac": ((hw / (tc_ms / 1e3)) / 1e12 / peak_bf16) if tc_ms > 0 else None,
         "share_of_step": tc_ms / ms if ms > 0 else None,
         "slicing_share_of_step": sl_ms / ms if ms > 0 else None,
+        "inverse_elimination_share_of_step": inv_ms / ms if ms > 0 else None,
         "traffic": (TC_DRAM_BYTES_PER_ITEM_B400 * (alg / max(n_launch, 1)) / (8.0 * WORK["b"] ** 3)
-                    if WORK["b"] == 400 and n_launch else None),
+                    if TC_DRAM_BYTES_PER_ITEM_B400 and WORK["b"] == 400 and n_launch else None),
         "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
     }
     line = {
@@ -387,7 +394,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORK["name"], "points_per_step": P, "precision": args.precision,
                    "l2": "inputs > L2: each step streams 358 MB of H blocks",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "tc_config": tuned},
         "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roofline,
     }
     if rank == 0 and not args.no_extras:

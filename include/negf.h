@@ -64,6 +64,10 @@ typedef enum {
 #define NEGF_PT_NONFINITE 4     /* an output of this point is NaN or Inf                    */
 #define NEGF_PT_BAD_INDEX 8     /* sys_idx / e_idx out of range: the point was clamped to a
                                    valid row and its results are meaningless               */
+#define NEGF_PT_TIMEOUT 16      /* mixed form: a bounded wait inside a tensor-core GEMM of the
+                                   call gave up after 2 s (that GEMM's outputs are NaN, so the
+                                   point is also NEGF_PT_NONFINITE); set for every point of
+                                   the chunk of points that was being solved                */
 
 typedef enum {
   NEGF_PREC_FP64 = 0,  /* every block operation in FP64 on the CUDA cores (reference form) */
@@ -254,10 +258,13 @@ negf_status negf_zinv_batched_noalloc(int32_t n_batch, int32_t n, double* M, dou
 
 /* ---- tensor-core GEMM configuration (autotuning) ----------------------------------------
  * The mixed-precision GEMM has negf_tc_config_count() kernel configurations, differing only in
- * speed: configuration c uses (4, 5, 6)[c / 2] pipeline stages and splits K into at most
- * (4, 8)[c % 2] exactly accumulated parts (more parts allow wider slices and fewer slice
- * products).  negf_tc_config_set selects one process-wide (default 4); results agree to the
- * GEMM's rounding.  The package's autotuner times them per block size and stores the choice. */
+ * speed: configuration c uses the kernel shape c / 2 of
+ *   (6 stages, 1 CTA, 1), (6, 1, 2), (6, 1, 3), (8 stages, CTA pair, 1), (8, 2, 2), (8, 2, 4)
+ * = (shared-memory pipeline stages, CTAs per MMA: one 128-row tile or a pair of CTAs with a
+ * 256-row MMA, stages released per MMA commit) and splits K into at most (4, 8)[c % 2] exactly
+ * accumulated parts (more parts allow wider slices and fewer slice products).
+ * negf_tc_config_set selects one process-wide (default 0); results agree to the GEMM's
+ * rounding.  The package's autotuner times them per block size and stores the choice. */
 int32_t negf_tc_config_count(void);
 negf_status negf_tc_config_set(int32_t idx);
 int32_t negf_tc_config_get(void);
@@ -265,9 +272,12 @@ int32_t negf_tc_config_get(void);
 /* ---- accounting ----------------------------------------------------------------------------
  * Instrumentation for benchmarks, not part of the method.  negf_launch_count() is the number
  * of kernels this library has launched since it was loaded.  With profiling on, every launch of
- * the tensor-core GEMM kernel (kind 0) and of its operand slicing (kind 1) is bracketed by CUDA
- * events on its own stream; negf_profile_read synchronises those events and returns the
- * cumulative launches and milliseconds of the kind since the last negf_profile_reset. */
+ * the tensor-core GEMM kernel (kind 0), of its operand slicing (kind 1) and every Gauss-Jordan
+ * elimination of a block inverse inside the sweeps (kind 2: the FP32 start of the mixed form or
+ * the whole FP64 inverse, without the Newton-Schulz products, which count as kinds 0 and 1) is
+ * bracketed by CUDA events on its own stream; negf_profile_read synchronises those events and
+ * returns the cumulative launches and milliseconds of the kind since the last
+ * negf_profile_reset. */
 void negf_profile_enable(int32_t on);
 void negf_profile_reset(void);
 negf_status negf_profile_read(int32_t kind, long long* launches, double* total_ms);
@@ -275,6 +285,9 @@ negf_status negf_profile_read(int32_t kind, long long* launches, double* total_m
  * and the BF16 tensor-core flops actually issued (all slice products over the padded tiles). */
 negf_status negf_profile_flops(int32_t kind, double* algorithmic, double* hardware);
 long long negf_launch_count(void);
+/* Name of the last CUDA runtime error that made a call of this library return NEGF_ERR_CUDA
+ * (e.g. "cudaErrorInvalidValue"; "cudaSuccess" if none), for diagnostics.  Static string. */
+const char* negf_last_cuda_error(void);
 
 #ifdef __cplusplus
 }

@@ -26,6 +26,7 @@ from .negf import (  # noqa: F401
     tc_config_count,
     rgf,
     PROF_SLICE,
+    PROF_INV,
     workspace_size,
     library,
     PREC_FP64,

@@ -119,7 +119,7 @@ void carve_adj(char* base, size_t& off, int P, int b, int N, int prec, AdjWs& w)
 #define CK(x)                                    \
   do {                                           \
     cudaError_t e_ = (x);                        \
-    if (e_ != cudaSuccess) return NEGF_ERR_CUDA; \
+    if (e_ != cudaSuccess) return note_error(e_), NEGF_ERR_CUDA; \
   } while (0)
 
 struct AdjArgs {
@@ -152,6 +152,7 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   AdjWs w;
   carve_adj(wsbase, off, P, b, N, a.opt->precision, w);
   Engine eng(s, a.opt, w.eng, b, dev->n_sys);
+  CK(eng.timeout_reset());
   CK(launch_clamp_index(s, P, a.sys, dev->n_sys, w.sys, a.status));
   const int32_t* sysc = w.sys;
   const int32_t* erow = nullptr;
@@ -332,7 +333,9 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   }
   k_sum_points<<<(NB + kT - 1) / kT, kT, 0, s>>>(P, NB, w.vb, a.Vbar, a.accumulate ? 1 : 0);
   count_launch();
-  return cudaGetLastError() == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
+  CK(cudaGetLastError());
+  CK(eng.timeout_flag(P, a.status));
+  return NEGF_OK;
 }
 
 constexpr size_t kAdjBudget = 32ull << 30;

@@ -1,6 +1,7 @@
 // Block-level entry points: the batched complex GEMM and block inverse that the sweeps are
 // built from, exposed for callers that assemble their own recursions.
 #include "engine.cuh"
+#include "profile.cuh"
 #include "tc_gemm.cuh"
 
 using namespace negf;
@@ -54,7 +55,7 @@ negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, in
     tc_ws_carve(base, off, n_batch, M, N, K, tw);
     e = tc_gemm(s, n_batch, M, N, K, al, a, opA, b, opB, be, c, zero, none, false, nullptr, tw);
   }
-  return e == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
+  return note_error(e) == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
 }
 
 size_t negf_zinv_workspace_size(int32_t precision, int32_t n_batch, int32_t n) {
@@ -87,9 +88,12 @@ negf_status negf_zinv_batched(int32_t precision, int32_t n_batch, int32_t n, dou
   o.refine_steps = refine_steps;
   Engine eng(s, &o, w, n);
   const long long nn = (long long)n * n;
-  cudaError_t e = eng.inv(n_batch, BM<double>{reinterpret_cast<z64*>(M), nn, nullptr, n},
-                          BM<double>{reinterpret_cast<z64*>(X), nn, nullptr, n}, status, nullptr);
-  return e == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
+  cudaError_t e = eng.timeout_reset();
+  if (e == cudaSuccess)
+    e = eng.inv(n_batch, BM<double>{reinterpret_cast<z64*>(M), nn, nullptr, n},
+                BM<double>{reinterpret_cast<z64*>(X), nn, nullptr, n}, status, nullptr);
+  if (e == cudaSuccess) e = eng.timeout_flag(n_batch, status);
+  return note_error(e) == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -91,10 +91,24 @@ cudaError_t Engine::gemm(int P, int M, int N, int K, z64 alpha, BMc<double> A, i
   return gemm_simt<double>(s, P, M, N, K, alpha, A, opA, B, opB, beta, C, gamma, D, active);
 }
 
+cudaError_t Engine::timeout_reset() {
+  if (opt->precision != NEGF_PREC_MIXED) return cudaSuccess;
+  return tc_timeout_reset(s, tc_view(w, 1, b));
+}
+
+cudaError_t Engine::timeout_flag(int P, int32_t* status) {
+  if (opt->precision != NEGF_PREC_MIXED) return cudaSuccess;
+  return tc_timeout_flag(s, tc_view(w, 1, b), P, status);
+}
+
 cudaError_t Engine::inv(int P, BM<double> Mm, BM<double> X, int32_t* status,
                         const int32_t* active) {
-  if (opt->precision != NEGF_PREC_MIXED)
-    return gj_inverse<double>(s, P, b, Mm, X, w.invU, w.invT, w.piv, status, active);
+  if (opt->precision != NEGF_PREC_MIXED) {
+    prof_begin(s, PROF_INV);
+    cudaError_t e = gj_inverse<double>(s, P, b, Mm, X, w.invU, w.invT, w.piv, status, active);
+    prof_end(s, PROF_INV);
+    return e;
+  }
   // FP32 Gauss-Jordan start X0, then X <- X + X (I - M X) with tensor-core products
   const long long bb = (long long)b * b, n = (long long)P * bb;
   if (Mm.idx || X.idx || Mm.stride != bb || X.stride != bb || Mm.ld != b || X.ld != b)
@@ -104,7 +118,9 @@ cudaError_t Engine::inv(int P, BM<double> Mm, BM<double> X, int32_t* status,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   BM<float> m32{w.m32, bb, nullptr, b}, x32{w.x32, bb, nullptr, b};
+  prof_begin(s, PROF_INV);
   e = gj_inverse<float>(s, P, b, m32, x32, w.invU32, w.invT32, w.piv, status, active);
+  prof_end(s, PROF_INV);
   if (e != cudaSuccess) return e;
   k_to64<<<nblk(n), 256, 0, s>>>(n, w.x32, X.p, active, bb);
   count_launch();

@@ -41,6 +41,10 @@ struct Engine {
   cudaError_t gemm(int P, int M, int N, int K, z64 alpha, BMc<double> A, int opA, BMc<double> B,
                    int opB, z64 beta, BM<double> C, z64 gamma, BMc<double> D,
                    const int32_t* active);
+  // Mixed form: clear the tensor-core GEMM's timeout word / OR NEGF_PT_TIMEOUT into
+  // status[0..P) if a GEMM since the reset gave up a bounded wait.  No-ops in the FP64 form.
+  cudaError_t timeout_reset();
+  cudaError_t timeout_flag(int P, int32_t* status);
   // X = Mm^-1 for P items of size b (Mm is destroyed); zero pivots flag status[item].
   cudaError_t inv(int P, BM<double> Mm, BM<double> X, int32_t* status, const int32_t* active);
 };

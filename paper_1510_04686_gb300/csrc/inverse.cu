@@ -24,102 +24,118 @@ __device__ __forceinline__ double mag2(cx<R> a) {
   return (double)a.re * (double)a.re + (double)a.im * (double)a.im;
 }
 
-// Block-wide argmax of |col[r]|^2 over r in [r0, n) (ties -> lowest r).  Returns the row.
-template <typename R>
-__device__ int block_argmax(const cx<R>* col, int stride, int r0, int n, double* sv, int* si) {
-  double best = -1.0;
-  int bi = n;
-  for (int r = r0 + threadIdx.x; r < n; r += blockDim.x) {
-    double v = mag2(col[(long long)r * stride]);
-    if (v > best) {
-      best = v;
-      bi = r;
-    }
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    double ov = __shfl_down_sync(0xffffffffu, best, off);
-    int oi = __shfl_down_sync(0xffffffffu, bi, off);
-    if (ov > best || (ov == best && oi < bi)) {
-      best = ov;
-      bi = oi;
-    }
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) {
-    sv[w] = best;
-    si[w] = bi;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = blockDim.x >> 5;
-    double b = sv[0];
-    int i = si[0];
-    for (int k = 1; k < nw; ++k)
-      if (sv[k] > b || (sv[k] == b && si[k] < i)) {
-        b = sv[k];
-        i = si[k];
-      }
-    si[0] = (i >= n) ? r0 : i;
-  }
-  __syncthreads();
-  int res = si[0];
-  __syncthreads();
-  return res;
-}
-
+// 1 / a in FP64, flagging an exactly zero pivot (replaced by a tiny number so the sweep goes on).
 template <typename R>
 __device__ __forceinline__ cx<R> pivot_recip(cx<R> a, int32_t* st) {
   z64 ad = mkc<double>((double)a.re, (double)a.im);
   if (ad.re == 0.0 && ad.im == 0.0) {
-    if (threadIdx.x == 0 && st) atomicOr(st, NEGF_PT_SINGULAR);
+    if (st) atomicOr(st, NEGF_PT_SINGULAR);
     ad.re = sizeof(R) == 8 ? 1e-300 : 1e-30;
   }
   z64 d = crecip(ad);
   return mkc<R>((R)d.re, (R)d.im);
 }
 
-// One Gauss-Jordan step on column jj of an (rows x w) shared-memory array P (row stride w)
-// whose pivot row is `j`.  Uses f[rows] scratch.  Thread t works on column t % w of rows
-// t / w, t / w + blockDim / w, ... (no index division in the loops).
+// Per-CTA scratch of one Gauss-Jordan column step.
 template <typename R>
-__device__ void gj_step(cx<R>* P, int rows, int w, int j, int jj, cx<R>* f, int32_t* st) {
-  for (int r = threadIdx.x; r < rows; r += blockDim.x) f[r] = P[(long long)r * w + jj];
-  __syncthreads();
-  const cx<R> d = pivot_recip(f[j], st);
-  for (int c = threadIdx.x; c < w; c += blockDim.x) {
-    cx<R>& e = P[(long long)j * w + c];
-    e = (c == jj) ? d : e * d;
+struct GjScratch {
+  double sv[32];
+  int si[32];
+  cx<R> d;
+};
+
+// One Gauss-Jordan step on column jj of the shared-memory array P (rows x w, row stride w):
+// pivot search over rows [j, rows) (largest |m|^2 compared in FP64, lowest row on ties), swap
+// of rows j and the pivot row, pivot reciprocal in FP64, and elimination of column jj from all
+// other rows.  f[rows] and prow[w] are shared scratch.  Three block barriers per column:
+//   (1) after the per-warp argmax, (2) after the swap / column copy / reciprocal, (3) after the
+//   update.  Every thread combines the per-warp winners itself, and the elimination scales the
+//   pivot row on the fly from an unscaled copy, so no further barrier is needed.
+// Returns the pivot row.
+template <typename R>
+__device__ int gj_column(cx<R>* P, int rows, int w, int j, int jj, cx<R>* f, cx<R>* prow,
+                         GjScratch<R>& sc, int32_t* st) {
+  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  double best = -1.0;
+  int bi = rows;
+  for (int r = j + tid; r < rows; r += bd) {
+    const double v = mag2(P[(long long)r * w + jj]);
+    if (v > best) {
+      best = v;
+      bi = r;
+    }
   }
-  __syncthreads();
-  if (w <= (int)blockDim.x) {
-    const int c = threadIdx.x % w;
-    const int r0 = threadIdx.x / w, rstep = blockDim.x / w;
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, best, off);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+    if (ov > best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
+  }
+  if (lane == 0) {
+    sc.sv[wid] = best;
+    sc.si[wid] = bi;
+  }
+  __syncthreads();  // (1)
+  double b = sc.sv[0];
+  int pi = sc.si[0];
+  const int nw = bd >> 5;
+  for (int k = 1; k < nw; ++k)
+    if (sc.sv[k] > b || (sc.sv[k] == b && sc.si[k] < pi)) {
+      b = sc.sv[k];
+      pi = sc.si[k];
+    }
+  const int pr = (pi >= rows) ? j : pi;
+  // swap rows j <-> pr, keep the unscaled pivot row, copy column jj (as it is after the swap)
+  for (int c = tid; c < w; c += bd) {
+    const cx<R> a = P[(long long)j * w + c], v = P[(long long)pr * w + c];
+    P[(long long)j * w + c] = v;
+    P[(long long)pr * w + c] = a;
+    prow[c] = v;
+    if (c == jj) {
+      f[j] = v;
+      f[pr] = a;
+      sc.d = pivot_recip(v, st);
+    }
+  }
+  for (int r = tid; r < rows; r += bd)
+    if (r != j && r != pr) f[r] = P[(long long)r * w + jj];
+  __syncthreads();  // (2)
+  const cx<R> d = sc.d;
+  if (w <= bd) {
+    const int c = tid % w;
+    const int r0 = tid / w, rstep = bd / w;
     if (r0 < rstep) {
-      const cx<R> pj = P[(long long)j * w + c];
+      const cx<R> pj = (c == jj) ? d : prow[c] * d;
       for (int r = r0; r < rows; r += rstep) {
-        if (r == j) continue;
-        const cx<R> fr = f[r];
         cx<R>* e = P + (long long)r * w + c;
-        if (c == jj) {
-          *e = mkc<R>(R(0), R(0)) - fr * d;
+        if (r == j) {
+          *e = pj;
         } else {
-          cx<R> v = *e;
-          v.re = v.re - (fr.re * pj.re - fr.im * pj.im);
-          v.im = v.im - (fr.re * pj.im + fr.im * pj.re);
-          *e = v;
+          const cx<R> fr = f[r];
+          if (c == jj) {
+            *e = mkc<R>(R(0), R(0)) - fr * d;
+          } else {
+            cx<R> v = *e;
+            v.re = v.re - (fr.re * pj.re - fr.im * pj.im);
+            v.im = v.im - (fr.re * pj.im + fr.im * pj.re);
+            *e = v;
+          }
         }
       }
     }
   } else {
     for (int r = 0; r < rows; ++r) {
-      if (r == j) continue;
       const cx<R> fr = f[r];
-      for (int c = threadIdx.x; c < w; c += blockDim.x) {
+      for (int c = tid; c < w; c += bd) {
+        const cx<R> pj = (c == jj) ? d : prow[c] * d;
         cx<R>* e = P + (long long)r * w + c;
-        if (c == jj) {
+        if (r == j) {
+          *e = pj;
+        } else if (c == jj) {
           *e = mkc<R>(R(0), R(0)) - fr * d;
         } else {
-          const cx<R> pj = P[(long long)j * w + c];
           cx<R> v = *e;
           v.re = v.re - (fr.re * pj.re - fr.im * pj.im);
           v.im = v.im - (fr.re * pj.im + fr.im * pj.re);
@@ -128,18 +144,8 @@ __device__ void gj_step(cx<R>* P, int rows, int w, int j, int jj, cx<R>* f, int3
       }
     }
   }
-  __syncthreads();
-}
-
-template <typename R>
-__device__ void swap_rows_smem(cx<R>* P, int w, int a, int b) {
-  if (a == b) return;
-  for (int c = threadIdx.x; c < w; c += blockDim.x) {
-    cx<R> t = P[(long long)a * w + c];
-    P[(long long)a * w + c] = P[(long long)b * w + c];
-    P[(long long)b * w + c] = t;
-  }
-  __syncthreads();
+  __syncthreads();  // (3)
+  return pr;
 }
 
 template <typename R>
@@ -150,19 +156,18 @@ __global__ void __launch_bounds__(kThreads) k_gj_small(int n, BM<R> Mm, BM<R> X,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* A = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* f = A + (size_t)n * n;
-  int* perm = reinterpret_cast<int*>(f + n);
+  cx<R>* prow = f + n;
+  int* perm = reinterpret_cast<int*>(prow + n);
   int* src = perm + n;
-  __shared__ double sv[32];
-  __shared__ int si[32];
+  __shared__ GjScratch<R> sc;
   int32_t* st = status ? status + p : nullptr;
   const cx<R>* m = bat(Mm, p);
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) A[e] = m[(long long)(e / n) * Mm.ld + e % n];
+  for (int r = 0; r < n; ++r)
+    for (int c = threadIdx.x; c < n; c += blockDim.x) A[r * n + c] = m[(long long)r * Mm.ld + c];
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    int pr = block_argmax(A + j, n, j, n, sv, si);
+    const int pr = gj_column(A, n, n, j, j, f, prow, sc, st);
     if (threadIdx.x == 0) perm[j] = pr;
-    swap_rows_smem(A, n, j, pr);
-    gj_step(A, n, n, j, j, f, st);
   }
   if (threadIdx.x == 0) {
     for (int c = 0; c < n; ++c) src[c] = c;
@@ -174,13 +179,17 @@ __global__ void __launch_bounds__(kThreads) k_gj_small(int n, BM<R> Mm, BM<R> X,
   }
   __syncthreads();
   cx<R>* x = bat(X, p);
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int r = e / n, c = e % n;
-    x[(long long)r * X.ld + c] = A[r * n + src[c]];
-  }
+  for (int r = 0; r < n; ++r)
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+      x[(long long)r * X.ld + c] = A[r * n + src[c]];
 }
 
 // Panel step of the blocked form: columns [k0, k0 + w) of A (n x n, in global memory).
+// The panel is eliminated in shared memory; then, for the columns outside the panel, one pass
+// per column (each column owned by one thread, so no barrier) moves the swapped rows to their
+// final place, copies the pivot rows into T and zeroes them in A.  The row swaps of the panel
+// only ever move a panel row's content to an outside row, so reading all sources before any
+// panel row is cleared is enough to apply them at once.
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_gj_panel(int n, int k0, int w, int nb, BM<R> Am,
                                                        cx<R>* U, cx<R>* T, int32_t* piv,
@@ -190,8 +199,10 @@ __global__ void __launch_bounds__(kThreads) k_gj_panel(int n, int k0, int w, int
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* P = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* f = P + (size_t)n * w;
-  __shared__ double sv[32];
-  __shared__ int si[32];
+  cx<R>* prow = f + n;
+  int* cont = reinterpret_cast<int*>(prow + w);  // [n] source row of each row's final content
+  int* spv = cont + n;                           // [w] pivot rows of this panel
+  __shared__ GjScratch<R> sc;
   int32_t* st = status ? status + p : nullptr;
   cx<R>* a = bat(Am, p);
   const long long ld = Am.ld;
@@ -200,40 +211,44 @@ __global__ void __launch_bounds__(kThreads) k_gj_panel(int n, int k0, int w, int
     const int c = threadIdx.x % w;
     if (threadIdx.x / w < (int)blockDim.x / w) P[(long long)r * w + c] = a[r * ld + k0 + c];
   }
+  for (int r = threadIdx.x; r < n; r += blockDim.x) cont[r] = r;
   __syncthreads();
   for (int jj = 0; jj < w; ++jj) {
     const int j = k0 + jj;
-    int pr = block_argmax(P + jj, w, j, n, sv, si);
-    if (threadIdx.x == 0) pv[j] = pr;
-    swap_rows_smem(P, w, j, pr);
-    gj_step(P, n, w, j, jj, f, st);
-  }
-  // row swaps on the columns outside the panel, in elimination order
-  for (int jj = 0; jj < w; ++jj) {
-    const int j = k0 + jj;
-    const int pr = pv[j];
-    if (pr != j) {
-      for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        if (c >= k0 && c < k0 + w) continue;
-        cx<R> t = a[j * ld + c];
-        a[j * ld + c] = a[pr * ld + c];
-        a[pr * ld + c] = t;
-      }
+    const int pr = gj_column(P, n, w, j, jj, f, prow, sc, st);
+    if (threadIdx.x == 0) {
+      pv[j] = pr;
+      spv[jj] = pr;
+      const int t = cont[j];
+      cont[j] = cont[pr];
+      cont[pr] = t;
     }
-    __syncthreads();
   }
-  // T = pivot rows (panel columns zeroed); those rows of A are cleared outside the panel
+  __syncthreads();
   cx<R>* Tp = T + (long long)p * nb * n;
-  for (int jj = 0; jj < w; ++jj) {
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-      cx<R>* ae = a + (long long)(k0 + jj) * ld + c;
-      if (c >= k0 && c < k0 + w) {
-        Tp[(long long)jj * n + c] = mkc<R>(R(0), R(0));
-      } else {
-        Tp[(long long)jj * n + c] = *ae;
-        *ae = mkc<R>(R(0), R(0));
-      }
+  const cx<R> zero = mkc<R>(R(0), R(0));
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    if (c >= k0 && c < k0 + w) {
+      for (int jj = 0; jj < w; ++jj) Tp[(long long)jj * n + c] = zero;
+      continue;
     }
+    // (1) final pivot rows -> T, read before anything of this column is written
+    for (int j0 = 0; j0 < w; j0 += 8) {
+      cx<R> v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < w) v[u] = a[(long long)cont[k0 + j0 + u] * ld + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < w) Tp[(long long)(j0 + u) * n + c] = v[u];
+    }
+    // (2) rows below the panel that took part in a swap receive a panel row's content
+    for (int jj = 0; jj < w; ++jj) {
+      const int r = spv[jj];
+      if (r >= k0 + w) a[(long long)r * ld + c] = a[(long long)cont[r] * ld + c];
+    }
+    // (3) the pivot rows are cleared outside the panel
+    for (int jj = 0; jj < w; ++jj) a[(long long)(k0 + jj) * ld + c] = zero;
   }
   cx<R>* Up = U + (long long)p * n * nb;
   for (int r = threadIdx.x / w; r < n; r += blockDim.x / w) {
@@ -274,14 +289,20 @@ __global__ void __launch_bounds__(kThreads) k_gj_unpermute(int n, BM<R> Am, BM<R
 
 }  // namespace
 
-bool gj_fits_small(int n, int elem_bytes) {
-  size_t need = (size_t)n * n * elem_bytes + (size_t)n * elem_bytes + 2 * n * sizeof(int);
-  return need <= kSmemBudget;
+static size_t small_smem(int n, int elem_bytes) {
+  return (size_t)n * n * elem_bytes + 2 * (size_t)n * elem_bytes + 2 * n * sizeof(int);
+}
+static size_t panel_smem(int n, int w, int elem_bytes) {
+  return (size_t)n * w * elem_bytes + (size_t)n * elem_bytes + (size_t)w * elem_bytes +
+         (size_t)(n + w) * sizeof(int);
 }
 
+bool gj_fits_small(int n, int elem_bytes) { return small_smem(n, elem_bytes) <= kSmemBudget; }
+
 int gj_panel_width(int n, int elem_bytes) {
-  size_t per_col = (size_t)n * elem_bytes;
-  int w = (int)std::min<size_t>(32, (kSmemBudget - (size_t)n * elem_bytes) / per_col);
+  size_t per_col = (size_t)n * elem_bytes + elem_bytes + sizeof(int);
+  size_t fixed = (size_t)n * (elem_bytes + sizeof(int));
+  int w = fixed >= kSmemBudget ? 1 : (int)std::min<size_t>(32, (kSmemBudget - fixed) / per_col);
   int p2 = 1;
   while (p2 * 2 <= w) p2 *= 2;
   return std::max(1, p2);
@@ -293,7 +314,7 @@ cudaError_t gj_inverse(cudaStream_t s, int P, int n, BM<R> M, BM<R> X, cx<R>* U,
   if (P <= 0 || n <= 0) return cudaSuccess;
   const int eb = (int)sizeof(cx<R>);
   if (gj_fits_small(n, eb)) {
-    size_t smem = (size_t)n * n * eb + (size_t)n * eb + 2 * n * sizeof(int);
+    size_t smem = small_smem(n, eb);
     cudaError_t e = cudaFuncSetAttribute(k_gj_small<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBudget + 1024);
     if (e != cudaSuccess) return e;
@@ -307,7 +328,7 @@ cudaError_t gj_inverse(cudaStream_t s, int P, int n, BM<R> M, BM<R> X, cx<R>* U,
   if (e != cudaSuccess) return e;
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int w = std::min(nb, n - k0);
-    size_t smem = (size_t)n * w * eb + (size_t)n * eb;
+    size_t smem = panel_smem(n, w, eb);
     k_gj_panel<R><<<P, kThreads, smem, s>>>(n, k0, w, nb, M, U, T, piv, status, active);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

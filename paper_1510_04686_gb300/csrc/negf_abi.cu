@@ -7,6 +7,7 @@
 
 #include "common.cuh"
 #include "engine.cuh"
+#include "profile.cuh"
 #include "rgf_kernels.cuh"
 
 using namespace negf;
@@ -16,7 +17,7 @@ namespace {
 #define CK(x)                                  \
   do {                                         \
     cudaError_t e_ = (x);                      \
-    if (e_ != cudaSuccess) return NEGF_ERR_CUDA; \
+    if (e_ != cudaSuccess) return note_error(e_), NEGF_ERR_CUDA; \
   } while (0)
 
 const BMc<double> kNone{nullptr, 0, nullptr, 0};
@@ -161,6 +162,7 @@ negf_status lead_chunk_run(const negf_device* dev, int P, const double* E, const
   LeadWs w;
   carve_lead(c, P, b, opt, w);
   Engine eng(s, opt, w.eng, b, dev->n_sys);
+  CK(eng.timeout_reset());
   CK(launch_clamp_index(s, P, sys_in, dev->n_sys, w.sys, status));
   const int32_t* sys = w.sys;
   BMc<double> Hd{reinterpret_cast<const z64*>(dev->H_diag), (long long)(N * bb), sys, b};
@@ -222,6 +224,7 @@ negf_status lead_chunk_run(const negf_device* dev, int P, const double* E, const
                         flat(sigL, bb, b)));
   CK(launch_sr_status(s, P, w.active, w.item_status, w.iters, iters, opt->sr_max_iter, status));
   CK(launch_check_finite(s, reinterpret_cast<const double*>(sigR), (long long)4 * bb, P, status));
+  CK(eng.timeout_flag(P, status));
   return NEGF_OK;
 }
 
@@ -256,6 +259,7 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
   RgfWs w;
   carve_rgf(c, P, b, N, a.opt, w);
   Engine eng(s, a.opt, w.eng, b, dev->n_sys);
+  CK(eng.timeout_reset());
   const double eta = a.opt->eta_device;
   CK(launch_clamp_index(s, P, a.sys, dev->n_sys, w.sys, a.status));
   const int32_t* sysc = w.sys;
@@ -367,6 +371,7 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
   if (a.density) CK(launch_check_finite(s, a.density, NB, P, a.status));
   if (a.current && N > 1) CK(launch_check_finite(s, a.current, N - 1, P, a.status));
   if (a.transmission) CK(launch_check_finite(s, a.transmission, 1, P, a.status));
+  CK(eng.timeout_flag(P, a.status));
   return NEGF_OK;
 }
 

@@ -17,11 +17,11 @@ struct Pending {
 };
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_pool;
-cudaEvent_t g_open[PROF_KINDS] = {nullptr, nullptr};
-long long g_count[PROF_KINDS] = {0, 0};
-double g_ms[PROF_KINDS] = {0.0, 0.0};
-double g_alg[PROF_KINDS] = {0.0, 0.0};
-double g_hw[PROF_KINDS] = {0.0, 0.0};
+cudaEvent_t g_open[PROF_KINDS] = {};
+long long g_count[PROF_KINDS] = {};
+double g_ms[PROF_KINDS] = {};
+double g_alg[PROF_KINDS] = {};
+double g_hw[PROF_KINDS] = {};
 
 cudaEvent_t get_event() {
   if (!g_pool.empty()) {
@@ -36,6 +36,14 @@ cudaEvent_t get_event() {
 }  // namespace
 
 void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+namespace {
+std::atomic<int> g_last_err{0};
+}
+cudaError_t note_error(cudaError_t e) {
+  if (e != cudaSuccess) g_last_err.store((int)e);
+  return e;
+}
 bool profiling_on() { return g_prof.load(std::memory_order_relaxed) != 0; }
 
 void prof_begin(cudaStream_t s, int kind) {
@@ -68,6 +76,10 @@ using namespace negf;
 extern "C" {
 
 void negf_profile_enable(int32_t on) { g_prof.store(on ? 1 : 0); }
+
+const char* negf_last_cuda_error(void) {
+  return cudaGetErrorName(static_cast<cudaError_t>(g_last_err.load()));
+}
 
 long long negf_launch_count(void) { return g_launches.load(); }
 

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "profile.cuh"
@@ -21,7 +22,8 @@ constexpr int kKC = 64;       // real K elements per stage (128 bytes of BF16 pe
 constexpr int kMaxItems = 240;
 constexpr int kThreads = 320;  // warps 0-7 epilogue, warp 8 TMA producer, warp 9 MMA issuer
 constexpr int kEpiWarps = 8;
-constexpr int kNT = 128;       // tile columns (real); TMEM: 2 accumulators + FP32-pair sums
+constexpr int kNT = 128;       // tile columns (real)
+constexpr int kAccBufs = 2;    // TMEM: 2 accumulators + the hi and lo words of the running sums
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on every device wait
 
 constexpr int kMaxParts = 8;
@@ -136,9 +138,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
         "=r"(r[31])
       : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_ld_wait() {
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x32.b32"
@@ -150,6 +149,12 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
       "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
       "r"(r[29]), "r"(r[30]), "r"(r[31])
       : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 // (double)x * 2^k from the bit pattern of the FP32 number x with integer operations only
 // (exact; x normal or zero, result in the normal double range).  FP64 arithmetic is scarce on
@@ -163,9 +168,6 @@ __device__ __forceinline__ double f32_scaled(uint32_t xb, int k) {
   return __longlong_as_double((long long)(sign | e64 | man));
 }
 
-__device__ __forceinline__ void tmem_st_wait() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
 
 // ------------------------------------------------------------------ slicing kernels
 template <typename T>
@@ -188,150 +190,273 @@ __device__ __forceinline__ int scale_exp(double mx) {
   return e;
 }
 
-// S fixed-point slices of x * 2^-e (|.| < 1): slice s holds q_s 2^(-beta s) with integer q_s,
-// |q_1| <= 2^beta, |q_s| <= 2^(beta-1) afterwards, so that every slice is exact in BF16.
-// Integer arithmetic only: |x| 2^(62-e) as a 62-bit fixed-point number, then rounded base-2^beta
-// digits taken from the top.
-__device__ __forceinline__ void cut(double x, int e, int S, int beta, float* out) {
+// Fixed-point slicing of one value.  x 2^(beta - e) (|x| < 2^e) is rounded once to the integer
+// R = round(|x| 2^(beta S - e)) < 2^(beta S) + 1 and written in balanced base-2^beta digits
+// q_0 .. q_{S-1} (value sum_s q_s 2^(-beta s)): q_0 in [0, 2^beta], q_s in [-2^(beta-1),
+// 2^(beta-1)) for s >= 1.  Adding H = 2^(beta-1) to every digit position below the top one turns
+// the balanced digits into plain bit fields of R + H (minus 2^(beta-1)), so each digit is a
+// constant shift and mask.  Every q_s 2^(-beta s) is exact in BF16.
+template <int BETA, int S>
+struct Digits {
+  static constexpr int kBits = BETA * S;
+  static_assert(kBits <= 56, "fixed-point value must fit 64 bits with headroom");
+  static constexpr unsigned long long kH = [] {
+    unsigned long long h = 0;
+    for (int s = 1; s < S; ++s) h |= (1ull << (BETA - 1)) << (BETA * (S - 1 - s));
+    return h;
+  }();
+};
+
+// R + H for |x| with line exponent e, and the sign of x.
+template <int BETA, int S>
+__device__ __forceinline__ unsigned long long fixed_point(double x, int e, bool& neg) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  neg = (u >> 63) != 0;
   const int ex = (int)((u >> 52) & 0x7FF);
   unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
   if (ex) mant |= 1ull << 52;
-  const int sh = (ex ? ex : 1) - 1075 + 62 - e;  // |x| 2^(62-e) = mant 2^sh
-  long long R;
+  const int sh = (ex ? ex : 1) - 1075 + Digits<BETA, S>::kBits - e;  // |x| 2^(beta S - e) = mant 2^sh
+  unsigned long long R;
   if (mant == 0 || sh <= -64) {
     R = 0;
   } else if (sh >= 0) {
-    R = (long long)(mant << sh);
+    R = mant << sh;
   } else {
     const int r = -sh;
-    R = (long long)((mant + (1ull << (r - 1))) >> r);
+    R = (mant + (1ull << (r - 1))) >> r;
   }
-  const bool neg = (u >> 63) != 0;
-  float scale = 1.0f;
-  const float step = __int_as_float((127 - beta) << 23);  // 2^-beta
-  for (int s = 0; s < S; ++s) {
-    const int shs = 62 - beta * (s + 1);
-    const long long q = (R + (1ll << (shs - 1))) >> shs;
-    R -= q << shs;
-    const float v = (float)(int)q * scale;  // |q| <= 2^8: exact through a 32-bit integer
-    out[s] = neg ? -v : v;
-    scale *= step;
-  }
+  return R + Digits<BETA, S>::kH;
 }
 
+// Slice s of a value from its R + H: sign * q_s * 2^(-beta s) as FP32 (exact).
+template <int BETA, int S, int SI>
+__device__ __forceinline__ float digit(unsigned long long RH, bool neg) {
+  constexpr int pos = BETA * (S - 1 - SI);
+  int q = (SI == 0) ? (int)(RH >> pos) : (int)((RH >> pos) & ((1ull << BETA) - 1)) - (1 << (BETA - 1));
+  // |q| <= 2^8: exact through the 1.5 * 2^23 bias
+  float f = __int_as_float(0x4B400000 + q) - 12582912.0f;
+  f *= __int_as_float((127 - BETA * SI) << 23);  // 2^(-beta s)
+  return neg ? -f : f;
+}
+
+constexpr int kTK = 32;  // complex K values per tile
 constexpr int kMaxS = 12;
 
-// Slicing of 32 "lines" per CTA (rows of op(A), or columns of op(B)) with coalesced reads: the
-// operand is read in 32 x 32 complex tiles through shared memory, so a line that is a column in
-// memory costs the same as a row.  Pass 1 finds each line's scale exponent, pass 2 writes the S
-// slices.  A lines become one output row [Re, Im, Re, Im, ...]; B lines (columns n of op(B))
-// become the two rows 2n = [Re, -Im, ...] and 2n + 1 = [Im, Re, ...] of the real embedding.
-template <bool kB>
-__global__ void __launch_bounds__(256) k_slice(int n_lines, int K, int L, int S, int beta,
-                                               BMc<double> X, int op, bool line_is_col,
-                                               __nv_bfloat16* out, int32_t* eo,
-                                               const int32_t* active) {
+template <int S>
+struct Unroll {
+  template <class F>
+  __device__ __forceinline__ static void run(F&& f) {
+    Unroll<S - 1>::run(f);
+    f(std::integral_constant<int, S - 1>{});
+  }
+};
+template <>
+struct Unroll<0> {
+  template <class F>
+  __device__ __forceinline__ static void run(F&&) {}
+};
+
+// Slicing of 32 "lines" per CTA (rows of op(A), or columns of op(B)).  Pass 1 finds each line's
+// scale exponent with coalesced reads along the line's memory layout; pass 2 walks 32 x 32
+// complex tiles through shared memory (so a line that is a column in memory costs the same as a
+// row) and writes the S slices with 16-byte stores.  A lines become one output row
+// [Re, Im, Re, Im, ...]; B lines (columns n of op(B)) become the two rows 2n = [Re, -Im, ...]
+// and 2n + 1 = [Im, Re, ...] of the real embedding.  Padding columns up to L are written as 0.
+template <bool kB, int BETA, int S>
+__global__ void __launch_bounds__(256) k_slice(int n_lines, int K, int L, BMc<double> X, int op,
+                                               bool line_is_col, __nv_bfloat16* out,
+                                               int32_t* eo, const int32_t* active) {
   const int p = blockIdx.y;
   if (active && !active[p]) return;
-  __shared__ z64 tile[32][33];
+  __shared__ z64 tile[32][kTK + 1];
+  __shared__ unsigned long long smax[8][32];
   __shared__ int sexp[32];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int l0 = blockIdx.x * 32;
   const z64* x = bat(X, p);
   const long long ld = X.ld;
   const bool conj = (op == OP_C);
-  auto load_tile = [&](int k0) {
-    // 32 lines x 32 k values; lanes run along the contiguous index of memory
-    for (int e = threadIdx.x; e < 1024; e += 256) {
-      const int a = e >> 5, bidx = e & 31;  // a: slow index, bidx: fast (contiguous) index
-      int li, k;
-      if (line_is_col) {
-        k = a;
-        li = bidx;  // memory x[k][line]
-      } else {
-        li = a;
-        k = bidx;   // memory x[line][k]
-      }
-      const int line = l0 + li, kk = k0 + k;
-      z64 v = mkc(0.0, 0.0);
-      if (line < n_lines && kk < K)
-        v = line_is_col ? x[(long long)kk * ld + line] : x[(long long)line * ld + kk];
-      tile[li][k] = v;
-    }
-  };
-  unsigned long long mb[4] = {0, 0, 0, 0};
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    load_tile(k0);
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const z64 v = tile[w + 8 * j][lane];
-      mb[j] = max(mb[j], max(absbits(v.re), absbits(v.im)));
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const unsigned long long m = warp_max(mb[j]);
-    const int line = l0 + w + 8 * j;
-    if (lane == 0) {
-      const int e = scale_exp(__longlong_as_double((long long)m));
-      sexp[w + 8 * j] = e;
-      if (line < n_lines) eo[(long long)p * n_lines + line] = e;
-    }
-  }
-  __syncthreads();
-  const long long rows_out = kB ? 2LL * n_lines : (long long)n_lines;
-  float sr[kMaxS], si[kMaxS];
-  for (int k0 = 0; k0 < L / 2; k0 += 32) {
-    if (k0 < K) load_tile(k0);
-    __syncthreads();
+
+  // ---- pass 1: max |Re|, |Im| over each line (bit patterns compare as magnitudes)
+  if (!line_is_col) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int li = w + 8 * j, line = l0 + li;
-      const int k2 = k0 + lane;
-      if (line >= n_lines) continue;
-      z64 v = (k0 < K) ? tile[li][lane] : mkc(0.0, 0.0);
-      if (conj) v.im = -v.im;
-      const int e = sexp[li];
-      cut(v.re, e, S, beta, sr);
-      cut(v.im, e, S, beta, si);
-      for (int s = 0; s < S; ++s) {
-        __nv_bfloat16* base = out + ((long long)p * S + s) * rows_out * L;
-        if (!kB) {
-          __nv_bfloat162 pr;
-          pr.x = __float2bfloat16_rn(sr[s]);
-          pr.y = __float2bfloat16_rn(si[s]);
-          reinterpret_cast<__nv_bfloat162*>(base + (long long)line * L)[k2] = pr;
-        } else {
-          __nv_bfloat162 r0, r1;
-          r0.x = __float2bfloat16_rn(sr[s]);
-          r0.y = __float2bfloat16_rn(-si[s]);
-          r1.x = __float2bfloat16_rn(si[s]);
-          r1.y = __float2bfloat16_rn(sr[s]);
-          reinterpret_cast<__nv_bfloat162*>(base + (2LL * line) * L)[k2] = r0;
-          reinterpret_cast<__nv_bfloat162*>(base + (2LL * line + 1) * L)[k2] = r1;
+      unsigned long long m = 0;
+      if (line < n_lines) {
+        const z64* row = x + (long long)line * ld;
+        for (int k = lane; k < K; k += 32) {
+          const z64 v = row[k];
+          m = max(m, max(absbits(v.re), absbits(v.im)));
         }
       }
+      m = warp_max(m);
+      if (lane == 0) smax[0][li] = m;
+    }
+  } else {
+    const int line = l0 + lane;
+    unsigned long long m = 0;
+    if (line < n_lines)
+      for (int k = w; k < K; k += 8) {
+        const z64 v = x[(long long)k * ld + line];
+        m = max(m, max(absbits(v.re), absbits(v.im)));
+      }
+    smax[w][lane] = m;
+    __syncthreads();
+    if (w == 0) {
+      unsigned long long mm = smax[0][lane];
+#pragma unroll
+      for (int i = 1; i < 8; ++i) mm = max(mm, smax[i][lane]);
+      smax[0][lane] = mm;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int li = threadIdx.x, line = l0 + li;
+    const int e = scale_exp(__longlong_as_double((long long)smax[0][li]));
+    sexp[li] = e;
+    if (line < n_lines) eo[(long long)p * n_lines + line] = e;
+  }
+  __syncthreads();
+
+  // ---- pass 2: tiles of 32 lines x 32 complex K values.  Thread (li, g) converts the four
+  // values k = 4g .. 4g + 3 of line li; lanes 0-7 of a quarter-warp hold eight different lines
+  // (conflict-free shared-memory reads), and the four quarter-warps cover 16 consecutive k.
+  const int li = (w & 3) * 8 + (lane & 7);
+  const int g = (w >> 2) * 4 + (lane >> 3);
+  const int line = l0 + li;
+  const int e = sexp[li];
+  const long long rows_out = kB ? 2LL * n_lines : (long long)n_lines;
+  for (int k0 = 0; k0 < L / 2; k0 += kTK) {
+    if (k0 < K) {
+      for (int t = threadIdx.x; t < 32 * kTK; t += 256) {
+        const int a = t >> 5, c = t & 31;  // a: slow index, c: fast (contiguous) index
+        int tl, tk;
+        if (line_is_col) {
+          tk = a;
+          tl = c;  // memory x[k][line]
+        } else {
+          tl = a;
+          tk = c;  // memory x[line][k]
+        }
+        const int ln = l0 + tl, kk = k0 + tk;
+        z64 v = mkc(0.0, 0.0);
+        if (ln < n_lines && kk < K)
+          v = line_is_col ? x[(long long)kk * ld + ln] : x[(long long)ln * ld + kk];
+        tile[tl][tk] = v;
+      }
+    }
+    __syncthreads();
+    if (line < n_lines) {
+      unsigned long long rr[4], ri[4];
+      bool nr[4], ni[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        z64 v = (k0 < K) ? tile[li][4 * g + j] : mkc(0.0, 0.0);
+        if (conj) v.im = -v.im;
+        rr[j] = fixed_point<BETA, S>(v.re, e, nr[j]);
+        ri[j] = fixed_point<BETA, S>(v.im, e, ni[j]);
+      }
+      const long long col = 2LL * (k0 + 4 * g);  // first BF16 column of this thread's 4 values
+      Unroll<S>::run([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        __nv_bfloat16* base = out + ((long long)p * S + s) * rows_out * L;
+        uint32_t w0[4], w1[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float fr = digit<BETA, S, s>(rr[j], nr[j]);
+          const float fi = digit<BETA, S, s>(ri[j], ni[j]);
+          __nv_bfloat162 a, b2;
+          if (!kB) {
+            a = __floats2bfloat162_rn(fr, fi);
+          } else {
+            a = __floats2bfloat162_rn(fr, -fi);
+            b2 = __floats2bfloat162_rn(fi, fr);
+            w1[j] = *reinterpret_cast<uint32_t*>(&b2);
+          }
+          w0[j] = *reinterpret_cast<uint32_t*>(&a);
+        }
+        if (!kB) {
+          *reinterpret_cast<uint4*>(base + (long long)line * L + col) =
+              make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        } else {
+          *reinterpret_cast<uint4*>(base + (2LL * line) * L + col) =
+              make_uint4(w0[0], w0[1], w0[2], w0[3]);
+          *reinterpret_cast<uint4*>(base + (2LL * line + 1) * L + col) =
+              make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        }
+      });
     }
     __syncthreads();
   }
 }
 
 // ------------------------------------------------------------------ MMA kernel
-template <int NT, int STAGES>
+// CG = 1: one CTA computes a 128-row tile with tcgen05.mma.cta_group::1 (M = 128).
+// CG = 2: a cluster of two x-adjacent CTAs (consecutive row tiles) computes a 256-row tile with
+// tcgen05.mma.cta_group::2 (M = 256) issued by the even CTA: each CTA loads its own 128 rows of
+// A and one half of the B tile (NT / 2 rows of the embedded B), so a stage moves 24 KB per CTA
+// instead of 32 KB, and each CTA's tensor memory receives the accumulator of its own rows.  Both
+// CTAs' loads complete on the even CTA's barrier; the MMA commits arrive on both CTAs' barriers.
+template <int NT, int STAGES, int CG, int G>
 struct Cfg {
+  static_assert(STAGES % G == 0, "stages are released in whole groups");
   static constexpr int kStages = STAGES;
+  static constexpr int kGroups = STAGES / G;                  // stage groups (one commit each)
   static constexpr int kATile = kBM * kKC * 2;                // 16 KB
-  static constexpr int kBTile = NT * kKC * 2;
+  static constexpr int kBRows = NT / CG;                      // rows of the B tile this CTA loads
+  static constexpr int kBTile = kBRows * kKC * 2;
   static constexpr int kStage = kATile + kBTile;
   static constexpr int kStagingPerWarp = 32 * 8 * 16;         // 32 rows x 8 complex outputs
   static constexpr int kStaging = kEpiWarps * kStagingPerWarp;
   static constexpr int kSmem = kStages * kStage + kStaging + 1024 + 256;  // + align + barriers
 };
 
-template <int NT, int STAGES>
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the variable at local shared address `a` in CTA `rank`
+__device__ __forceinline__ uint32_t map_rank(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" :::
+                   "memory");
+}
+// TMA load whose completion is counted on an mbarrier of this CTA or of its peer (cta_group::2)
+__device__ __forceinline__ void tma_load_3d_pair(void* dst, const CUtensorMap* map,
+                                                 uint32_t bar_cluster, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem_d, uint64_t a, uint64_t b,
+                                              uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+// commit of the pair's MMAs, arriving on the barrier at this offset in both CTAs
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster)
+               : "memory");
+}
+
+template <int NT, int STAGES, int CG, int G>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const Sched sched, int M, int N2, int S, int two_beta,
@@ -340,48 +465,58 @@ __global__ void __launch_bounds__(kThreads, 1)
               int zmodeB, z64 alpha,
               z64 beta, z64 gamma, BM<double> C, BMc<double> D, int add_identity,
               const int32_t* active, int32_t* err) {
-  static_assert(NT == 128, "TMEM holds 2 x NT accumulator columns + 2 x NT sum columns");
-  using CF = Cfg<NT, STAGES>;
+  static_assert(NT * (kAccBufs + 2) == 512, "TMEM: kAccBufs accumulators + hi / lo sum words");
+  static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair per MMA");
+  using CF = Cfg<NT, STAGES, CG, G>;
   constexpr int kStages = CF::kStages;
   const int p = blockIdx.z;
+  // both CTAs of a pair have the same item, so they leave together (before any cluster barrier)
   if (active && !active[p]) return;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   z64* staging = reinterpret_cast<z64*>(smem + kStages * CF::kStage);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * CF::kStage + CF::kStaging);
-  uint64_t* empty = full + kStages;
-  uint64_t* accfull = empty + kStages;
-  uint64_t* accempty = accfull + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accempty + 2);
+  uint64_t* empty = full + kStages;  // one per group of G stages
+  uint64_t* accfull = empty + CF::kGroups;
+  uint64_t* accempty = accfull + kAccBufs;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accempty + kAccBufs);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * NT, m0 = blockIdx.y * kBM;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * NT;  // pairs are adjacent along x
+  const uint32_t rank = (CG == 2) ? cluster_rank() : 0u;
+  const bool leader = (rank == 0);
   // slice set of this batch item: its own (mode 0), the indexed one (1) or the shared one (2)
   const int zA = zmodeA == 0 ? p : (zmodeA == 1 ? zidxA[p] : 0);
   const int zB = zmodeB == 0 ? p : (zmodeB == 1 ? zidxB[p] : 0);
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
-    }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1);
+    for (int i = 0; i < CF::kGroups; ++i) mbar_init(&empty[i], 1);
+    for (int i = 0; i < kAccBufs; ++i) {
       mbar_init(&accfull[i], 1);
-      mbar_init(&accempty[i], kEpiWarps * 32);
+      mbar_init(&accempty[i], CG * kEpiWarps);  // one arrival per epilogue warp of the pair
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 9) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                     smem_u32(tmem_slot))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (CG == 2) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                       smem_u32(tmem_slot))
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                       smem_u32(tmem_slot))
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
     tc_fence_before();
   }
   __syncthreads();
+  if constexpr (CG == 2) cluster_sync();  // the peer's barriers exist before any remote use
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -393,41 +528,60 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int ii = 0; ii < sched.n_items && !*abort_flag; ++ii) {
         const Item it = sched.it[ii];
         for (int kc = sched.part_lo[it.kp]; kc < sched.part_hi[it.kp]; ++kc) {
-          if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
+          // a group of G stages is released by one MMA commit: wait at the group's first stage
+          if (stage % G == 0 && !mbar_wait(&empty[stage / G], phase ^ 1, abort_flag)) break;
           unsigned char* st = smem + stage * CF::kStage;
-          mbar_expect_tx(&full[stage], CF::kATile + CF::kBTile);
-          tma_load_3d(st, &mapA, &full[stage], kc * kKC, m0, zA * S + it.s - 1);
-          tma_load_3d(st + CF::kATile, &mapB, &full[stage], kc * kKC, n0, zB * S + it.t - 1);
+          if constexpr (CG == 2) {
+            // both CTAs' loads of this stage complete on the even CTA's barrier
+            if (leader) mbar_expect_tx(&full[stage], CG * CF::kStage);
+            const uint32_t fb = map_rank(smem_u32(&full[stage]), 0);
+            tma_load_3d_pair(st, &mapA, fb, kc * kKC, m0, zA * S + it.s - 1);
+            tma_load_3d_pair(st + CF::kATile, &mapB, fb, kc * kKC, n0 + (int)rank * CF::kBRows,
+                             zB * S + it.t - 1);
+          } else {
+            mbar_expect_tx(&full[stage], CF::kStage);
+            tma_load_3d(st, &mapA, &full[stage], kc * kKC, m0, zA * S + it.s - 1);
+            tma_load_3d(st + CF::kATile, &mapB, &full[stage], kc * kKC, n0, zB * S + it.t - 1);
+          }
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1;
           }
         }
       }
-      for (int i = 0; i < kStages; ++i) {  // drain loads still in flight (bounded)
-        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
-        if (++stage == kStages) {
+      // drain: wait (bounded) until every stage group holding loads was released by the MMAs
+      if (stage % G != 0) {
+        stage += G - stage % G;
+        if (stage == kStages) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      for (int i = 0; i < CF::kGroups; ++i) {
+        if (!mbar_wait(&empty[stage / G], phase ^ 1, abort_flag)) break;
+        stage += G;
+        if (stage == kStages) {
           stage = 0;
           phase ^= 1;
         }
       }
     }
   } else if (warp == 9) {
-    // ---------------- MMA issuer
-    if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kBM, NT);
+    // ---------------- MMA issuer (the even CTA of a pair issues for both)
+    if (lane == 0 && leader) {
+      const uint32_t idesc = idesc_bf16(kBM * CG, NT);
       int stage = 0;
       uint32_t phase = 0;
       int cur = -1;
       uint32_t acc_on = 0;
       for (int ii = 0; ii < sched.n_items && !*abort_flag; ++ii) {
         const Item it = sched.it[ii];
-        const int buf = it.acc & 1;
+        const int buf = it.acc % kAccBufs;
         if (it.acc != cur) {
           cur = it.acc;
           acc_on = 0;
-          if (cur >= 2) {
-            if (!mbar_wait(&accempty[buf], ((cur >> 1) - 1) & 1, abort_flag)) break;
+          if (cur >= kAccBufs) {  // the buffer's previous group must have been read out
+            if (!mbar_wait(&accempty[buf], ((cur / kAccBufs) - 1) & 1, abort_flag)) break;
             tc_fence_after();
           }
         }
@@ -442,11 +596,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t a0 = smem_u32(smem + stage * CF::kStage);
 #pragma unroll
           for (int k = 0; k < kKC / 16; ++k) {
-            mma_bf16(dcol, sw128_desc(a0 + 32 * k), sw128_desc(a0 + CF::kATile + 32 * k), idesc,
-                     acc_on);
+            if constexpr (CG == 2)
+              mma_bf16_pair(dcol, sw128_desc(a0 + 32 * k), sw128_desc(a0 + CF::kATile + 32 * k),
+                            idesc, acc_on);
+            else
+              mma_bf16(dcol, sw128_desc(a0 + 32 * k), sw128_desc(a0 + CF::kATile + 32 * k), idesc,
+                       acc_on);
             acc_on = 1;
           }
-          mma_commit(&empty[stage]);
+          if (stage % G == G - 1) {  // last stage of its group: release the group
+            if constexpr (CG == 2)
+              mma_commit_pair(&empty[stage / G]);
+            else
+              mma_commit(&empty[stage / G]);
+          }
           if (++stage == kStages) {
             stage = 0;
             phase ^= 1;
@@ -454,7 +617,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!ok) break;
         const bool last_of_acc = (ii + 1 == sched.n_items) || (sched.it[ii + 1].acc != cur);
-        if (last_of_acc) mma_commit(&accfull[buf]);
+        if (last_of_acc) {
+          if constexpr (CG == 2)
+            mma_commit_pair(&accfull[buf]);
+          else
+            mma_commit(&accfull[buf]);
+        }
+      }
+      // the last, partly used stage group is released too (the producer's drain waits for it)
+      if (!*abort_flag && stage % G != 0) {
+        if constexpr (CG == 2)
+          mma_commit_pair(&empty[stage / G]);
+        else
+          mma_commit(&empty[stage / G]);
       }
     }
   } else {
@@ -474,10 +649,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool unit_gamma = (gamma.re == 1.0 && gamma.im == 0.0);
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int cbase = half * (NT / 2);
-    const uint32_t t_hi = tmem + lane_off + 2 * NT, t_lo = tmem + lane_off + 3 * NT;
+    const uint32_t t_hi = tmem + lane_off + kAccBufs * NT, t_lo = t_hi + NT;
     for (int acc = 0; acc < sched.n_acc; ++acc) {
-      const int buf = acc & 1;
-      if (!mbar_wait(&accfull[buf], (acc >> 1) & 1, abort_flag)) break;
+      const int buf = acc % kAccBufs;
+      if (!mbar_wait(&accfull[buf], (acc / kAccBufs) & 1, abort_flag)) break;
       tc_fence_after();
       const bool last = (acc == sched.n_acc - 1);
       for (int c0 = cbase; c0 < cbase + NT / 2; c0 += 32) {
@@ -549,13 +724,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       tmem_st_wait();
       tc_fence_before();
-      mbar_arrive(&accempty[buf]);
+      __syncwarp();
+      if (lane == 0) {  // the warp is done with this accumulator (and its sums are stored)
+        if constexpr (CG == 2)
+          mbar_arrive_cluster(map_rank(smem_u32(&accempty[buf]), 0));
+        else
+          mbar_arrive(&accempty[buf]);
+      }
+    }
+    if (*abort_flag && row_ok) {
+      // a bounded wait gave up: this tile's outputs are NaN, so that the caller's finite checks
+      // see the failure instead of stale values
+      const double qnan = __longlong_as_double(0x7FF8000000000000LL);
+      z64* crow = bat(C, p) + (long long)m * C.ld;
+      for (int n = (n0 + cbase) / 2; n < (n0 + cbase + NT / 2) / 2 && n < N; ++n)
+        crow[n] = mkc(qnan, qnan);
     }
   }
   __syncthreads();
+  // the pair leaves together: no MMA of the even CTA may still reach the odd CTA's memory
+  if constexpr (CG == 2) cluster_sync();
   if (warp == 9) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    if constexpr (CG == 2)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
+                   : "memory");
   }
   if (threadIdx.x == 0 && *abort_flag && err) atomicExch(err, 1);
 }
@@ -609,16 +805,16 @@ Sched build_sched(int S, int n_chunks, int n_parts) {
   return sc;
 }
 
-template <int NT, int STAGES>
+template <int NT, int STAGES, int CG, int G>
 cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S, int two_beta,
                       int n_parts, const CUtensorMap& mA, const CUtensorMap& mB, const TcWs& ws,
                       const int32_t* zA, int zmA, const int32_t* zB, int zmB, z64 alpha,
                       z64 beta, z64 gamma, BM<double> C, BMc<double> D, bool add_identity,
                       const int32_t* active) {
-  using CF = Cfg<NT, STAGES>;
+  using CF = Cfg<NT, STAGES, CG, G>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NT, STAGES>,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NT, STAGES, CG, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, CF::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -626,27 +822,50 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
   if ((long long)std::min(n_parts, kMaxParts) * S * (S + 1) / 2 > kMaxItems)
     return cudaErrorInvalidValue;  // schedule longer than the kernel's item table
   Sched sc = build_sched(S, L / kKC, n_parts);
-  dim3 grid((N2 + NT - 1) / NT, (M + kBM - 1) / kBM, P);
+  const int mt = (M + kBM - 1) / kBM;
+  // x: row tiles (a CTA pair is two x-adjacent CTAs, so the count is even for pairs), y: columns
+  dim3 grid((mt + CG - 1) / CG * CG, (N2 + NT - 1) / NT, P);
+  if (grid.y > 65535) return cudaErrorInvalidValue;
   {
     const double alg = 8.0 * M * (N2 / 2) * (double)K * P;
-    const double hw = 2.0 * grid.y * kBM * (double)grid.x * NT * L * (S * (S + 1) / 2) * P;
+    const double hw = 2.0 * grid.x * kBM * (double)grid.y * NT * L * (S * (S + 1) / 2) * P;
     prof_flops(PROF_TC_GEMM, alg, hw);
   }
   prof_begin(s, PROF_TC_GEMM);
-  k_tc_gemm<NT, STAGES><<<grid, kThreads, CF::kSmem, s>>>(
-      mA, mB, sc, M, N2, S, two_beta, ws.expA, ws.expB, zA, zmA, zB, zmB, alpha, beta, gamma, C,
-      D, add_identity ? 1 : 0, active, ws.err);
+  cudaLaunchConfig_t lc = {};
+  lc.gridDim = grid;
+  lc.blockDim = dim3(kThreads, 1, 1);
+  lc.dynamicSmemBytes = CF::kSmem;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CG;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&lc, k_tc_gemm<NT, STAGES, CG, G>, mA, mB, sc, M, N2, S,
+                                     two_beta, (const int32_t*)ws.expA, (const int32_t*)ws.expB,
+                                     zA, zmA, zB, zmB, alpha, beta, gamma, C, D,
+                                     add_identity ? 1 : 0, active, ws.err);
   prof_end(s, PROF_TC_GEMM);
   count_launch();
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 }  // namespace
 
-// Kernel configuration (autotuner knob): index = 2 * stage_choice + part_choice with
-// stage_choice 0/1/2 = 4/5/6 pipeline stages and part_choice 0/1 = at most 4/8 K parts.
-std::atomic<int> g_cfg{4};
-constexpr int kNumCfg = 6;
+// Kernel configuration (autotuner knob): index = 2 * shape + part_choice, part_choice 0/1 = at
+// most 4/8 K parts; shape = (pipeline stages, CTAs per MMA, stages released per MMA commit).
+// Every tcgen05.commit stalls the tensor pipe for a few hundred cycles, so releasing shared-
+// memory stages in groups (one commit per G stages) keeps the MMAs back to back.
+struct TcShape {
+  int stages, cg, grp;
+};
+constexpr TcShape kShapes[] = {{6, 1, 1}, {6, 1, 2}, {6, 1, 3}, {8, 2, 1}, {8, 2, 2}, {8, 2, 4}};
+constexpr int kNumCfg = 2 * (int)(sizeof(kShapes) / sizeof(kShapes[0]));
+std::atomic<int> g_cfg{0};
 
 void tc_plan(int K, int* beta, int* S, int* parts, int max_parts) {
   // Slices of beta bits, S = ceil(48 / beta), and the number of K parts such that every group
@@ -682,6 +901,45 @@ void tc_plan(int K, int* beta, int* S) {
   tc_plan(K, beta, S, &parts);
 }
 
+template <bool kB>
+cudaError_t launch_slice(cudaStream_t s, int beta, int S, dim3 grid, int n_lines, int K, int L,
+                         BMc<double> X, int op, bool line_is_col, __nv_bfloat16* out, int32_t* eo,
+                         const int32_t* active) {
+#define NEGF_SLICE_CASE(B_, S_)                                                        \
+  if (beta == B_ && S == S_) {                                                         \
+    k_slice<kB, B_, S_><<<grid, 256, 0, s>>>(n_lines, K, L, X, op, line_is_col, out, eo, \
+                                             active);                                  \
+    return cudaGetLastError();                                                         \
+  }
+  NEGF_SLICE_CASE(8, 6)
+  NEGF_SLICE_CASE(7, 7)
+  NEGF_SLICE_CASE(6, 8)
+  NEGF_SLICE_CASE(5, 10)
+  NEGF_SLICE_CASE(4, 12)
+  NEGF_SLICE_CASE(3, 12)
+  NEGF_SLICE_CASE(2, 12)
+#undef NEGF_SLICE_CASE
+  return cudaErrorInvalidValue;  // a (beta, S) pair tc_plan never produces
+}
+
+namespace {
+__global__ void k_flag_timeout(const int32_t* err, int P, int32_t* status) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < P && *err) atomicOr(status + p, NEGF_PT_TIMEOUT);
+}
+}  // namespace
+
+cudaError_t tc_timeout_reset(cudaStream_t s, const TcWs& ws) {
+  return cudaMemsetAsync(ws.err, 0, sizeof(int32_t), s);
+}
+
+cudaError_t tc_timeout_flag(cudaStream_t s, const TcWs& ws, int P, int32_t* status) {
+  if (P <= 0 || !status) return cudaSuccess;
+  k_flag_timeout<<<(P + 255) / 256, 256, 0, s>>>(ws.err, P, status);
+  count_launch();
+  return cudaGetLastError();
+}
+
 size_t tc_ws_bytes(int P, int M, int N, int K) {
   size_t off = 0;
   TcWs w;
@@ -704,11 +962,11 @@ void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, TcWs& w) {
     off = a + bytes;
     return base ? base + a : nullptr;
   };
+  w.err = static_cast<int32_t*>(take(256));  // first, so that its place does not depend on P
   w.slicesA = take((size_t)P * S * M * L * 2);
   w.slicesB = take((size_t)P * S * 2 * N * L * 2);
   w.expA = static_cast<int32_t*>(take((size_t)P * M * 4));
   w.expB = static_cast<int32_t*>(take((size_t)P * N * 4));
-  w.err = static_cast<int32_t*>(take(256));
 }
 
 cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<double> A,
@@ -739,8 +997,10 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
   // with a shared operand the active mask cannot gate the slicing by item
   const int32_t* actA = zmA == 0 ? active : nullptr;
   const int32_t* actB = zmB == 0 ? active : nullptr;
-  int bta, S;
-  tc_plan(K, &bta, &S);
+  const int cfg = g_cfg.load();
+  const int CG = kShapes[cfg / 2].cg;
+  int bta, S, parts;
+  tc_plan(K, &bta, &S, &parts, cfg % 2 == 0 ? 4 : 8);
   const int L = round_up(2 * K, kKC);
   const int N2 = 2 * N;
   __nv_bfloat16* sa = static_cast<__nv_bfloat16*>(ws.slicesA);
@@ -748,31 +1008,29 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
   prof_begin(s, PROF_SLICE);
   // a row of op(A) is a column of A in memory for op T/C; a column of op(B) is a column of B for
   // op N
-  k_slice<false><<<dim3((M + 31) / 32, PA), 256, 0, s>>>(M, K, L, S, bta, A, opA, opA != OP_N,
-                                                         sa, ws.expA, actA);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_slice<false>(s, bta, S, dim3((M + 31) / 32, PA), M, K, L, A, opA,
+                                      opA != OP_N, sa, ws.expA, actA);
   if (e != cudaSuccess) return e;
-  k_slice<true><<<dim3((N + 31) / 32, PB), 256, 0, s>>>(N, K, L, S, bta, B, opB, opB == OP_N, sb,
-                                                        ws.expB, actB);
+  e = launch_slice<true>(s, bta, S, dim3((N + 31) / 32, PB), N, K, L, B, opB, opB == OP_N, sb,
+                         ws.expB, actB);
   prof_end(s, PROF_SLICE);
   count_launch(2);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  int parts;
-  tc_plan(K, &bta, &S, &parts);
+  if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
   if (!make_map(&mA, sa, L, M, (long long)PA * S, kBM)) return cudaErrorInvalidValue;
-  if (!make_map(&mB, sb, L, N2, (long long)PB * S, kNT)) return cudaErrorInvalidValue;
-  switch (g_cfg.load() / 2) {
-    case 0:
-      return launch_tc<kNT, 4>(s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB,
-                               zmB, alpha, beta, gamma, C, D, add_identity, active);
-    case 1:
-      return launch_tc<kNT, 5>(s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB,
-                               zmB, alpha, beta, gamma, C, D, add_identity, active);
-    default:
-      return launch_tc<kNT, 6>(s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB,
-                               zmB, alpha, beta, gamma, C, D, add_identity, active);
+  if (!make_map(&mB, sb, L, N2, (long long)PB * S, kNT / CG)) return cudaErrorInvalidValue;
+#define NEGF_TC_ARGS                                                                          \
+  s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB, zmB, alpha, beta, gamma, C, D, \
+      add_identity, active
+  switch (cfg / 2) {
+    case 0: return launch_tc<kNT, 6, 1, 1>(NEGF_TC_ARGS);
+    case 1: return launch_tc<kNT, 6, 1, 2>(NEGF_TC_ARGS);
+    case 2: return launch_tc<kNT, 6, 1, 3>(NEGF_TC_ARGS);
+    case 3: return launch_tc<kNT, 8, 2, 1>(NEGF_TC_ARGS);
+    case 4: return launch_tc<kNT, 8, 2, 2>(NEGF_TC_ARGS);
+    default: return launch_tc<kNT, 8, 2, 4>(NEGF_TC_ARGS);
   }
+#undef NEGF_TC_ARGS
 }
 
 }  // namespace negf

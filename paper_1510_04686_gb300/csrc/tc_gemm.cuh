@@ -33,6 +33,12 @@ void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, TcWs& w);
 void tc_plan(int K, int* beta, int* S);
 void tc_plan(int K, int* beta, int* S, int* parts);
 
+// The device error word ws.err is set when a bounded wait inside the GEMM kernel gave up (the
+// tile's outputs are then NaN).  tc_timeout_reset zeroes it; tc_timeout_flag ORs
+// NEGF_PT_TIMEOUT into status[0..P) when it is set.  Both are asynchronous on s.
+cudaError_t tc_timeout_reset(cudaStream_t s, const TcWs& ws);
+cudaError_t tc_timeout_flag(cudaStream_t s, const TcWs& ws, int P, int32_t* status);
+
 // n_distinct: number of different matrices an indexed operand (idx != NULL) selects from
 // (0 = unknown: slice every item).
 cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<double> A,

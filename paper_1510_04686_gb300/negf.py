@@ -26,8 +26,9 @@ _STATUS = {
 
 
 class NegfError(RuntimeError):
-    def __init__(self, code, where):
-        super().__init__(f"{where}: negf status {code} ({_STATUS.get(code, 'unknown')})")
+    def __init__(self, code, where, detail=""):
+        msg = f"{where}: negf status {code} ({_STATUS.get(code, 'unknown')})"
+        super().__init__(msg + (f": {detail}" if detail else ""))
         self.code = code
 
 
@@ -50,7 +51,7 @@ EXPORTS = ("negf_default_options", "negf_abi_version", "negf_status_string",
            "negf_zgemm_batched", "negf_zinv_workspace_size", "negf_zinv_batched",
            "negf_profile_enable", "negf_profile_reset", "negf_profile_read", "negf_profile_flops",
            "negf_launch_count", "negf_zinv_batched_noalloc", "negf_tc_config_count",
-           "negf_tc_config_set", "negf_tc_config_get")
+           "negf_tc_config_set", "negf_tc_config_get", "negf_last_cuda_error")
 
 
 def library():
@@ -116,6 +117,8 @@ def library():
     lib.negf_tc_config_set.restype = c_int32
     lib.negf_tc_config_get.argtypes = []
     lib.negf_tc_config_get.restype = c_int32
+    lib.negf_last_cuda_error.argtypes = []
+    lib.negf_last_cuda_error.restype = ctypes.c_char_p
     _LIB = lib
     return lib
 
@@ -191,7 +194,10 @@ def workspace_size(dev: Device, n_pts: int, opt: _Opt, which: int) -> int:
 
 def _check(code, where):
     if code != 0:
-        raise NegfError(code, where)
+        detail = ""
+        if code == 2:  # NEGF_ERR_CUDA: name the CUDA runtime error behind it
+            detail = library().negf_last_cuda_error().decode()
+        raise NegfError(code, where, detail)
 
 
 def lead_selfenergy(dev: Device, E: torch.Tensor, sys_idx: torch.Tensor, opt: _Opt):
@@ -357,7 +363,7 @@ def zinv(M, precision=PREC_FP64, refine_steps=2):
     return X, st
 
 
-PROF_TC_GEMM, PROF_SLICE = 0, 1
+PROF_TC_GEMM, PROF_SLICE, PROF_INV = 0, 1, 2
 
 
 def profile(enable: bool):

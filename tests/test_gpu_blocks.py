@@ -34,7 +34,9 @@ def _bound(A, B, opA, opB):
     return K * a.max(axis=-1)[..., :, None] * b.max(axis=-2)[..., None, :]
 
 
-CASES = [(40, 40, 40), (77, 130, 50), (128, 128, 128), (200, 160, 96), (400, 400, 400)]
+# M = 300 has an odd number (3) of 128-row tiles, which the CTA-pair kernel pads to an even count
+CASES = [(40, 40, 40), (77, 130, 50), (128, 128, 128), (200, 160, 96), (300, 200, 150),
+         (400, 400, 400)]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -113,17 +115,17 @@ def test_zgemm_every_kernel_configuration():
     """All tensor-core kernel configurations (pipeline depth, K-part policy) give the product to
     the stated accuracy; the default is restored afterwards."""
     rng = np.random.default_rng(21)
-    nb, n = 3, 400
-    A = _rand(rng, (nb, n, n))
-    B = _rand(rng, (nb, n, n))
-    ref = A @ B
-    tol = 1e-13 * _bound(A, B, "N", "N")
-    At, Bt = torch.as_tensor(A, device="cuda"), torch.as_tensor(B, device="cuda")
     old = negf.tc_config()
     try:
-        for c in range(negf.tc_config_count()):
-            negf.tc_config(c)
-            C = negf.zgemm(At, Bt, precision=1).cpu().numpy()
-            assert np.all(np.abs(C - ref) <= tol), c
+        for nb, n in ((3, 400), (2, 300)):  # 4 and 3 row tiles (one CTA or a CTA pair per MMA)
+            A = _rand(rng, (nb, n, n))
+            B = _rand(rng, (nb, n, n))
+            ref = A @ B
+            tol = 1e-13 * _bound(A, B, "N", "N")
+            At, Bt = torch.as_tensor(A, device="cuda"), torch.as_tensor(B, device="cuda")
+            for c in range(negf.tc_config_count()):
+                negf.tc_config(c)
+                C = negf.zgemm(At, Bt, precision=1).cpu().numpy()
+                assert np.all(np.abs(C - ref) <= tol), (n, c)
     finally:
         negf.tc_config(old)
