@@ -32,9 +32,11 @@ WORK = dict(N=70, b=400, n_E=512, n_k=8, ge_frac=0.1, eta=1e-6, seed=1001,
 METRIC = "RGF energy-points/s (leads + forward/backward sweeps + observables + FP64 quadrature)"
 PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0)
 # DRAM bytes (read + write) of k_tc_gemm per 400 x 400 x 400 complex item, from the ncu capture
-# summarised in profiles/tc_gemm_b400_x64.md; None while the kernel has changed since that
-# capture.  The traffic of a launch scales with its items.
-TC_DRAM_BYTES_PER_ITEM_B400 = None
+# summarised in profiles/tc_gemm_b400_x64.md (64 items: 933.5 MB read + 153.8 MB written) of
+# tensor-core configuration TC_PROFILED_CONFIG; reported only when the bench runs that
+# configuration.  The traffic of a launch scales with its items.
+TC_DRAM_BYTES_PER_ITEM_B400 = (933.452032e6 + 153.795072e6) / 64
+TC_PROFILED_CONFIG = 0
 
 
 def parse():
@@ -49,13 +51,17 @@ def parse():
     ap.add_argument("--fp64-points", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU-oracle, FP64-GPU and end-to-end side measurements")
-    ap.add_argument("--workload", default="rgf", choices=["rgf", "scba", "adjoint", "ragged"],
-                    help="rgf: the throughput line above; scba / adjoint / ragged: side "
+    ap.add_argument("--workload", default="rgf",
+                    choices=["rgf", "scba", "adjoint", "ragged", "gemm"],
+                    help="rgf: the throughput line above; scba / adjoint / ragged / gemm: side "
                          "measurements of the Born loop (N=70, b=600), the adjoint sweep "
-                         "(b=3430) and ragged block sizes (b=200..800)")
+                         "(b=3430), ragged block sizes (b=200..800) and the batched tensor-core "
+                         "complex GEMM alone (b x b x b, --gemm-batch items)")
     ap.add_argument("--scba-energies", type=int, default=128)
     ap.add_argument("--adj-slabs", type=int, default=20)
     ap.add_argument("--ragged-points", type=int, default=16)
+    ap.add_argument("--gemm-b", type=int, default=400)
+    ap.add_argument("--gemm-batch", type=int, default=64)
     return ap.parse_args()
 
 
@@ -253,6 +259,27 @@ def run_side(args):
                     dtype="bf16-slices->fp32 (fp64 storage)",
                     config={"workload": f"adjoint, N={N} slabs x 3430 orbitals (343 atoms x 10),"
                                         " V ~ U(-0.3, 0.3) eV per atom, 1 point"})
+    elif args.workload == "gemm":
+        b, nb = args.gemm_b, args.gemm_batch
+        g = torch.Generator(device=dvc).manual_seed(1)
+        A = torch.randn((nb, b, b), dtype=torch.complex128, device=dvc, generator=g)
+        B = torch.randn((nb, b, b), dtype=torch.complex128, device=dvc, generator=g)
+        C = torch.empty_like(A)
+        negf.profile_reset()
+        negf.profile(True)
+        ms, _ = _timed(torch, lambda: negf.zgemm(A, B, C, precision=negf.PREC_MIXED),
+                       args.warmup, args.steps)
+        negf.profile(False)
+        n_tc, tc_ms, alg, hw = negf.profile_read(negf.PROF_TC_GEMM)
+        n_sl, sl_ms, _, _ = negf.profile_read(negf.PROF_SLICE)
+        line.update(metric="batched complex GEMM, algorithmic TFLOP/s (8 b^3 per item)",
+                    value=8.0 * b ** 3 * nb * args.steps / (ms / 1e3) / 1e12, unit="TFLOP/s",
+                    ms_per_step=ms / args.steps, dtype="bf16-slices->fp32 (fp64 in/out)",
+                    config={"workload": f"{nb} items of {b} x {b} x {b} complex128",
+                            "tc_config": negf.tc_config(),
+                            "tc_kernel_ms": tc_ms / max(n_tc, 1),
+                            "slicing_ms": sl_ms / max(n_sl, 1),
+                            "issued_bf16_tflops": hw / (tc_ms / 1e3) / 1e12 if tc_ms else None})
     else:
         N, npts = 70, args.ragged_points
         systems = []
@@ -383,7 +410,9 @@ def main():
         "slicing_share_of_step": sl_ms / ms if ms > 0 else None,
         "inverse_elimination_share_of_step": inv_ms / ms if ms > 0 else None,
         "traffic": (TC_DRAM_BYTES_PER_ITEM_B400 * (alg / max(n_launch, 1)) / (8.0 * WORK["b"] ** 3)
-                    if TC_DRAM_BYTES_PER_ITEM_B400 and WORK["b"] == 400 and n_launch else None),
+                    if TC_DRAM_BYTES_PER_ITEM_B400 and WORK["b"] == 400 and n_launch
+                    and prec == negf.PREC_MIXED and negf.tc_config() == TC_PROFILED_CONFIG
+                    else None),
         "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
     }
     line = {
