@@ -105,12 +105,13 @@ typedef struct {
                             many steps (after 8) and stop early; 0 = never read back: always run
                             sr_max_iter steps with converged points masked on the device, so the
                             call makes no host synchronisation (CUDA-graph capturable).  Default 4 */
-  int32_t reserved;
+  int32_t adjoint_segment; /* negf_rgf_adjoint: slabs per recomputed segment (sweep
+                            checkpointing); 0 = keep every slab's blocks.  Default 0 */
 } negf_options;
 
 /* Fill `opt` with the defaults (eta 1e-6 in leads and device, mu_L = +0.1, mu_R = -0.1,
  * kT = 0.025852, sr_tol = 1e-13, sr_max_iter = 100, FP64, refine_steps = 2, chunk = 0,
- * sr_host_check = 4). */
+ * sr_host_check = 4, adjoint_segment = 0). */
 void negf_default_options(negf_options* opt);
 
 int32_t negf_abi_version(void);
@@ -196,7 +197,11 @@ negf_status negf_scba_step(int32_t n_k, int32_t n_E, int32_t n_orb, const double
  *   density_bar [n_pts][N*b] (nullable), current_bar [n_pts][N-1] (nullable),
  * it accumulates V_bar[N][b] += sum_p sum_j density_bar[p][j] dn_j(p)/dV
  *                                 + sum_i current_bar[p][i] dj_i(p)/dV.
- * V_bar is device double [N][b] and is overwritten (not accumulated into).              */
+ * V_bar is device double [N][b] and is overwritten (not accumulated into).
+ * Memory: every slab's forward and backward blocks are kept (8 N b^2 complex per point in
+ * flight) unless opt->adjoint_segment = s with 0 < s < N: then only segment-boundary blocks are
+ * kept and one segment at a time is recomputed (3 N + 5 s + 4 N / s blocks per point, about
+ * 3 more forward sweeps and 1 more backward sweep); results agree to rounding.            */
 negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, const double* E,
                              const int32_t* sys_idx, const double* V, const double* sigma_R,
                              const double* sigma_L, const double* scat_R,

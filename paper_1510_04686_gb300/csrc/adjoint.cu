@@ -8,6 +8,16 @@
 //   M = ... - diag(V)  ->  Vbar_q = -Re Mbar_qq
 // with xbar = dL/dRe x + i dL/dIm x.  The backward sweep is reversed first (slab 0 upwards),
 // then the forward sweep (slab N-1 downwards).  Lead and scattering self-energies are held fixed.
+//
+// Sweep checkpointing (negf_options.adjoint_segment = s, 0 < s < N): the slabs are cut into
+// segments of s.  Only the forward values (g, g^<) of the last slab of every segment and the
+// backward values (G, G^<) of the first slab of every segment are kept; the blocks of one
+// segment at a time are recomputed from them, once for the backward sweep, once for its reverse
+// and once for the reverse of the forward sweep.  The cotangents of g, g^< and L stay
+// full-length (they are written by the reverse of the backward sweep in increasing slab order
+// and read by the reverse of the forward sweep in decreasing order), so the footprint drops
+// from 8 N to 3 N + 5 s + 4 N / s blocks per point, for 3 more forward sweeps and 1 more
+// backward sweep.  s = 0 (or s >= N) keeps every block and recomputes nothing.
 #include <algorithm>
 #include <vector>
 
@@ -87,26 +97,40 @@ T* take(char* base, size_t& off, size_t n) {
 
 struct AdjWs {
   int32_t *sys, *erow;
-  z64 *gF, *glF, *Gb, *GLb, *Lb, *gbar, *glbar, *Lbar;
+  z64 *gbar, *glbar, *Lbar;                      // cotangents, all slabs
+  z64 *sg, *sgl, *sL, *sG, *sGL;                 // blocks of the resident segment
+  z64 *ckg, *ckgl;                               // forward checkpoints: slab c s - 1
+  z64 *ckG, *ckGL;                               // backward checkpoints: slab (c + 1) s
   z64 *Gc, *Gn, *GLc, *GLn;                      // rolling cotangents of G, G^<
   z64 *t[14];                                    // temporaries
   double* vb;                                    // per-point V cotangent
   EngineWs eng;
 };
 
-void carve_adj(char* base, size_t& off, int P, int b, int N, int prec, AdjWs& w) {
+// Slabs per segment: the option, or every slab when it is 0 or >= N.
+int adj_segment(const negf_options* opt, int N) {
+  const int sg = opt->adjoint_segment;
+  return (sg <= 0 || sg >= N) ? N : sg;
+}
+
+void carve_adj(char* base, size_t& off, int P, int b, int N, int seg, int prec, AdjWs& w) {
   const size_t PB = (size_t)P * b * b;
   const size_t N1 = (size_t)std::max(N - 1, 1);
+  const size_t nseg = (size_t)((N + seg - 1) / seg);
   w.sys = take<int32_t>(base, off, P);
   w.erow = take<int32_t>(base, off, P);
-  w.gF = take<z64>(base, off, N * PB);
-  w.glF = take<z64>(base, off, N * PB);
-  w.Gb = take<z64>(base, off, N * PB);
-  w.GLb = take<z64>(base, off, N * PB);
-  w.Lb = take<z64>(base, off, N1 * PB);
   w.gbar = take<z64>(base, off, N * PB);
   w.glbar = take<z64>(base, off, N * PB);
   w.Lbar = take<z64>(base, off, N1 * PB);
+  w.sg = take<z64>(base, off, seg * PB);
+  w.sgl = take<z64>(base, off, seg * PB);
+  w.sL = take<z64>(base, off, seg * PB);
+  w.sG = take<z64>(base, off, seg * PB);
+  w.sGL = take<z64>(base, off, seg * PB);
+  w.ckg = take<z64>(base, off, nseg * PB);
+  w.ckgl = take<z64>(base, off, nseg * PB);
+  w.ckG = take<z64>(base, off, nseg * PB);
+  w.ckGL = take<z64>(base, off, nseg * PB);
   w.Gc = take<z64>(base, off, PB);
   w.Gn = take<z64>(base, off, PB);
   w.GLc = take<z64>(base, off, PB);
@@ -150,7 +174,9 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   const BMc<double> none{nullptr, 0, nullptr, 0};
   size_t off = 0;
   AdjWs w;
-  carve_adj(wsbase, off, P, b, N, a.opt->precision, w);
+  const int seg = adj_segment(a.opt, N);
+  const int nseg = (N + seg - 1) / seg;
+  carve_adj(wsbase, off, P, b, N, seg, a.opt->precision, w);
   Engine eng(s, a.opt, w.eng, b, dev->n_sys);
   CK(eng.timeout_reset());
   CK(launch_clamp_index(s, P, a.sys, dev->n_sys, w.sys, a.status));
@@ -183,55 +209,131 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   };
   const double eta = a.opt->eta_device;
 
-  // ------------------------------------------------ forward sweep (values kept)
-  for (int i = 0; i < N; ++i) {
-    BMc<double> Y = none;
-    if (i > 0) {
-      CK(eng.gemm(P, b, b, b, one, Fc(S(w.gF, i - 1)), OP_N, Hu(i - 1), OP_N, zero,
-                  F(S(w.Lb, i - 1)), zero, none, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Hu(i - 1), OP_C, Fc(S(w.Lb, i - 1)), OP_N, zero, F(T[0]), zero,
-                  none, nullptr));
-      Y = Fc(T[0]);
+  // ---- segment bookkeeping: which segment's forward / backward blocks are resident
+  int resF = -1, resB = -1;
+  auto seg_lo = [&](int c) { return c * seg; };
+  auto seg_hi = [&](int c) { return std::min(N, (c + 1) * seg); };
+  // forward blocks of slab i: the resident segment, or the checkpoint just below it
+  auto gF = [&](int i) -> z64* {
+    if (i >= seg_lo(resF) && i < seg_hi(resF)) return S(w.sg, i - seg_lo(resF));
+    return S(w.ckg, resF);  // i == seg_lo(resF) - 1
+  };
+  auto glF = [&](int i) -> z64* {
+    if (i >= seg_lo(resF) && i < seg_hi(resF)) return S(w.sgl, i - seg_lo(resF));
+    return S(w.ckgl, resF);
+  };
+  auto Lb = [&](int i) -> z64* { return S(w.sL, i - seg_lo(resF)); };
+  // backward blocks of slab i: the resident segment, or the checkpoint just above it
+  auto Gb = [&](int i) -> z64* {
+    if (i >= seg_lo(resB) && i < seg_hi(resB)) return S(w.sG, i - seg_lo(resB));
+    return S(w.ckG, resB);  // i == seg_hi(resB)
+  };
+  auto GLb = [&](int i) -> z64* {
+    if (i >= seg_lo(resB) && i < seg_hi(resB)) return S(w.sGL, i - seg_lo(resB));
+    return S(w.ckGL, resB);
+  };
+
+  // ---- forward sweep over segment c from the checkpoint below it (values kept for the
+  // segment; L_i = g_i t_i for every slab of the segment that has a right neighbour; the last
+  // slab's g, g^< become the checkpoint of segment c + 1)
+  auto forward_segment = [&](int c) -> negf_status {
+    if (resF == c) return NEGF_OK;
+    resF = c;
+    const int lo = seg_lo(c), hi = seg_hi(c);
+    for (int i = lo; i < hi; ++i) {
+      BMc<double> Y = none;
+      if (i > 0) {
+        // L_{i-1} = g_{i-1} t_{i-1} (kept when slab i - 1 is in the segment);  Y = t^H L
+        z64* Lprev = (i - 1 >= lo) ? Lb(i - 1) : T[6];
+        CK(eng.gemm(P, b, b, b, one, Fc(gF(i - 1)), OP_N, Hu(i - 1), OP_N, zero, F(Lprev), zero,
+                    none, nullptr));
+        CK(eng.gemm(P, b, b, b, one, Hu(i - 1), OP_C, Fc(Lprev), OP_N, zero, F(T[0]), zero, none,
+                    nullptr));
+        Y = Fc(T[0]);
+      }
+      CK(launch_assemble(s, P, b, a.E, eta, Hd(i), a.V ? a.V + (size_t)i * b : nullptr,
+                         a.scatR ? a.scatR + (size_t)i * b : nullptr, NB, erow, Y,
+                         i == 0 ? SigL_R : none, i == N - 1 ? SigR_R : none, F(T[1]), nullptr));
+      CK(eng.inv(P, F(T[1]), F(gF(i)), a.status, nullptr));
+      bool prev = false;
+      if (i > 0) {
+        CK(eng.gemm(P, b, b, b, one, Fc(gF(i)), OP_N, Hu(i - 1), OP_C, zero, F(T[2]), zero, none,
+                    nullptr));
+        CK(eng.gemm(P, b, b, b, one, Fc(glF(i - 1)), OP_N, Fc(T[2]), OP_C, zero, F(T[3]), zero,
+                    none, nullptr));
+        CK(eng.gemm(P, b, b, b, one, Fc(T[2]), OP_N, Fc(T[3]), OP_N, zero, F(glF(i)), zero, none,
+                    nullptr));
+        prev = true;
+      }
+      if (has_src(i)) {
+        CK(build_src(i, T[4]));
+        CK(eng.gemm(P, b, b, b, one, Fc(gF(i)), OP_N, Fc(T[4]), OP_N, zero, F(T[5]), zero, none,
+                    nullptr));
+        CK(eng.gemm(P, b, b, b, one, Fc(T[5]), OP_N, Fc(gF(i)), OP_C, prev ? one : zero,
+                    F(glF(i)), zero, none, nullptr));
+      } else if (!prev) {
+        CK(cudaMemsetAsync(glF(i), 0, PB * sizeof(z64), s));
+      }
     }
-    CK(launch_assemble(s, P, b, a.E, eta, Hd(i), a.V ? a.V + (size_t)i * b : nullptr,
-                       a.scatR ? a.scatR + (size_t)i * b : nullptr, NB, erow, Y,
-                       i == 0 ? SigL_R : none, i == N - 1 ? SigR_R : none, F(T[1]), nullptr));
-    CK(eng.inv(P, F(T[1]), F(S(w.gF, i)), a.status, nullptr));
-    bool prev = false;
-    if (i > 0) {
-      CK(eng.gemm(P, b, b, b, one, Fc(S(w.gF, i)), OP_N, Hu(i - 1), OP_C, zero, F(T[2]), zero,
-                  none, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(S(w.glF, i - 1)), OP_N, Fc(T[2]), OP_C, zero, F(T[3]), zero,
-                  none, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(T[2]), OP_N, Fc(T[3]), OP_N, zero, F(S(w.glF, i)), zero,
-                  none, nullptr));
-      prev = true;
+    if (hi - 1 <= N - 2)
+      CK(eng.gemm(P, b, b, b, one, Fc(gF(hi - 1)), OP_N, Hu(hi - 1), OP_N, zero, F(Lb(hi - 1)),
+                  zero, none, nullptr));
+    if (c + 1 < nseg) {
+      CK(cudaMemcpyAsync(S(w.ckg, c + 1), gF(hi - 1), PB * sizeof(z64),
+                         cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(S(w.ckgl, c + 1), glF(hi - 1), PB * sizeof(z64),
+                         cudaMemcpyDeviceToDevice, s));
     }
-    if (has_src(i)) {
-      CK(build_src(i, T[4]));
-      CK(eng.gemm(P, b, b, b, one, Fc(S(w.gF, i)), OP_N, Fc(T[4]), OP_N, zero, F(T[5]), zero,
-                  none, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(T[5]), OP_N, Fc(S(w.gF, i)), OP_C, prev ? one : zero,
-                  F(S(w.glF, i)), zero, none, nullptr));
-    } else if (!prev) {
-      CK(cudaMemsetAsync(S(w.glF, i), 0, PB * sizeof(z64), s));
+    return NEGF_OK;
+  };
+
+  // ---- backward sweep over segment c (its forward blocks resident) from the checkpoint above
+  // it; the segment's first slab becomes the checkpoint of segment c - 1
+  auto backward_segment = [&](int c) -> negf_status {
+    if (resB == c) return NEGF_OK;
+    resB = c;
+    const int lo = seg_lo(c), hi = seg_hi(c);
+    int top = hi - 1;
+    if (hi == N) {  // G_{N-1} = g_{N-1}, G^<_{N-1} = g^<_{N-1}
+      CK(cudaMemcpyAsync(Gb(N - 1), gF(N - 1), PB * sizeof(z64), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(GLb(N - 1), glF(N - 1), PB * sizeof(z64), cudaMemcpyDeviceToDevice, s));
+      top = N - 2;
     }
-  }
-  // ------------------------------------------------ backward sweep (into separate buffers)
-  CK(cudaMemcpyAsync(S(w.Gb, N - 1), S(w.gF, N - 1), PB * sizeof(z64), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(S(w.GLb, N - 1), S(w.glF, N - 1), PB * sizeof(z64), cudaMemcpyDeviceToDevice, s));
-  for (int i = N - 2; i >= 0; --i) {
-    z64 *Wm = T[0], *LW = T[1], *Q = T[2], *U = T[3];
-    CK(eng.gemm(P, b, b, b, one, Fc(S(w.Gb, i + 1)), OP_N, Hu(i), OP_C, zero, F(Wm), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(S(w.Lb, i)), OP_N, Fc(Wm), OP_N, zero, F(LW), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(LW), OP_N, Fc(S(w.gF, i)), OP_N, zero, F(S(w.Gb, i)), one,
-                Fc(S(w.gF, i)), nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(S(w.GLb, i + 1)), OP_N, Fc(S(w.Lb, i)), OP_C, zero, F(Q), zero,
-                none, nullptr));
-    CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_N, Fc(S(w.glF, i)), OP_N, zero, F(U), one, Fc(Q), nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(S(w.Lb, i)), OP_N, Fc(U), OP_N, zero, F(T[4]), one,
-                Fc(S(w.glF, i)), nullptr));
-    CK(launch_antiherm(s, P, b, Fc(T[4]), F(S(w.GLb, i)), nullptr));
+    for (int i = top; i >= lo; --i) {
+      z64 *Wm = T[0], *LW = T[1], *Q = T[2], *U = T[3];
+      CK(eng.gemm(P, b, b, b, one, Fc(Gb(i + 1)), OP_N, Hu(i), OP_C, zero, F(Wm), zero, none,
+                  nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(Lb(i)), OP_N, Fc(Wm), OP_N, zero, F(LW), zero, none,
+                  nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(LW), OP_N, Fc(gF(i)), OP_N, zero, F(Gb(i)), one,
+                  Fc(gF(i)), nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(GLb(i + 1)), OP_N, Fc(Lb(i)), OP_C, zero, F(Q), zero,
+                  none, nullptr));
+      CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_N, Fc(glF(i)), OP_N, zero, F(U), one, Fc(Q),
+                  nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(Lb(i)), OP_N, Fc(U), OP_N, zero, F(T[4]), one,
+                  Fc(glF(i)), nullptr));
+      CK(launch_antiherm(s, P, b, Fc(T[4]), F(GLb(i)), nullptr));
+    }
+    if (c > 0) {
+      CK(cudaMemcpyAsync(S(w.ckG, c - 1), Gb(lo), PB * sizeof(z64), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(S(w.ckGL, c - 1), GLb(lo), PB * sizeof(z64), cudaMemcpyDeviceToDevice,
+                         s));
+    }
+    return NEGF_OK;
+  };
+  negf_status r;
+#define RUN(x)                        \
+  do {                                \
+    if ((r = (x)) != NEGF_OK) return r; \
+  } while (0)
+
+  // ------------------------------------------------ forward sweep: checkpoints of every segment
+  for (int c = 0; c < nseg; ++c) RUN(forward_segment(c));
+  // ------------------------------------------------ backward sweep: checkpoints, top down
+  for (int c = nseg - 1; c >= 0; --c) {
+    RUN(forward_segment(c));
+    RUN(backward_segment(c));
   }
 
   // ------------------------------------------------ reverse of the backward sweep
@@ -243,14 +345,20 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   count_launch();
   z64 *Gc = w.Gc, *Gn = w.Gn, *GLc = w.GLc, *GLn = w.GLn;
   for (int i = 0; i + 1 < N; ++i) {
+    const int c = i / seg;
+    RUN(forward_segment(c));
+    if (resB != c) {
+      resB = -1;  // recompute the segment's backward blocks from its checkpoint
+      RUN(backward_segment(c));
+    }
     z64 *Wm = T[0], *LW = T[1], *Q = T[2], *U = T[3], *Sb = T[4], *Ub = T[5], *Wb = T[6],
         *Qb = T[7], *LWb = T[8];
-    z64* L = S(w.Lb, i);
+    z64* L = Lb(i);
     // recompute W, LW, Q, U of backward step i
-    CK(eng.gemm(P, b, b, b, one, Fc(S(w.Gb, i + 1)), OP_N, Hu(i), OP_C, zero, F(Wm), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(Gb(i + 1)), OP_N, Hu(i), OP_C, zero, F(Wm), zero, none, nullptr));
     CK(eng.gemm(P, b, b, b, one, Fc(L), OP_N, Fc(Wm), OP_N, zero, F(LW), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(S(w.GLb, i + 1)), OP_N, Fc(L), OP_C, zero, F(Q), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_N, Fc(S(w.glF, i)), OP_N, zero, F(U), one, Fc(Q), nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(GLb(i + 1)), OP_N, Fc(L), OP_C, zero, F(Q), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_N, Fc(glF(i)), OP_N, zero, F(U), one, Fc(Q), nullptr));
     // current cotangent: Ubar = Qbar = d_i t_i^H
     k_set_dtH<<<g2((long long)bb, P), kT, 0, s>>>(b, Hu(i), a.jbar ? a.jbar + i : nullptr, N - 1, F(Ub));
     k_set_dtH<<<g2((long long)bb, P), kT, 0, s>>>(b, Hu(i), a.jbar ? a.jbar + i : nullptr, N - 1, F(Qb));
@@ -262,7 +370,7 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
     CK(eng.gemm(P, b, b, b, one, Fc(Sb), OP_N, Fc(U), OP_C, one, F(S(w.Lbar, i)), zero, none, nullptr));
     CK(eng.gemm(P, b, b, b, one, Fc(L), OP_C, Fc(Sb), OP_N, one, F(Ub), zero, none, nullptr));
     // U = 2 W g^<_i + Q
-    CK(eng.gemm(P, b, b, b, two, Fc(Ub), OP_N, Fc(S(w.glF, i)), OP_C, zero, F(Wb), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, two, Fc(Ub), OP_N, Fc(glF(i)), OP_C, zero, F(Wb), zero, none, nullptr));
     CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_C, Fc(Ub), OP_N, one, F(S(w.glbar, i)), zero, none, nullptr));
     k_axpy<<<(unsigned)std::min<size_t>((PB + kT - 1) / kT, 4096), kT, 0, s>>>((long long)PB, Ub, Qb);
     count_launch();
@@ -270,12 +378,12 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
     k_seed_density<<<g2((long long)bb, P), kT, 0, s>>>(b, i + 1, NB, a.nbar, F(GLn));
     count_launch();
     CK(eng.gemm(P, b, b, b, one, Fc(Qb), OP_N, Fc(L), OP_N, one, F(GLn), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(Qb), OP_C, Fc(S(w.GLb, i + 1)), OP_N, one, F(S(w.Lbar, i)), zero,
+    CK(eng.gemm(P, b, b, b, one, Fc(Qb), OP_C, Fc(GLb(i + 1)), OP_N, one, F(S(w.Lbar, i)), zero,
                 none, nullptr));
     // G_i = g_i + LW g_i
     k_axpy<<<(unsigned)std::min<size_t>((PB + kT - 1) / kT, 4096), kT, 0, s>>>((long long)PB, Gc, S(w.gbar, i));
     count_launch();
-    CK(eng.gemm(P, b, b, b, one, Fc(Gc), OP_N, Fc(S(w.gF, i)), OP_C, zero, F(LWb), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(Gc), OP_N, Fc(gF(i)), OP_C, zero, F(LWb), zero, none, nullptr));
     CK(eng.gemm(P, b, b, b, one, Fc(LW), OP_C, Fc(Gc), OP_N, one, F(S(w.gbar, i)), zero, none, nullptr));
     // LW = L W
     CK(eng.gemm(P, b, b, b, one, Fc(LWb), OP_N, Fc(Wm), OP_C, one, F(S(w.Lbar, i)), zero, none, nullptr));
@@ -292,18 +400,19 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
 
   // ------------------------------------------------ reverse of the forward sweep
   for (int i = N - 1; i >= 0; --i) {
+    RUN(forward_segment(i / seg));
     z64 *K = T[0], *Vt = T[1], *Kb = T[2], *Vtb = T[3], *Ssrc = T[4], *Wsrc = T[5], *Wbar = T[6],
         *T1 = T[7], *Mb = T[8];
     z64* gb = S(w.gbar, i);
     z64* glb = S(w.glbar, i);
     if (i > 0) {
-      CK(eng.gemm(P, b, b, b, one, Fc(S(w.gF, i)), OP_N, Hu(i - 1), OP_C, zero, F(K), zero, none, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(S(w.glF, i - 1)), OP_N, Fc(K), OP_C, zero, F(Vt), zero, none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(gF(i)), OP_N, Hu(i - 1), OP_C, zero, F(K), zero, none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(glF(i - 1)), OP_N, Fc(K), OP_C, zero, F(Vt), zero, none, nullptr));
       // g^<_i = K Vt (+ source)
       CK(eng.gemm(P, b, b, b, one, Fc(glb), OP_N, Fc(Vt), OP_C, zero, F(Kb), zero, none, nullptr));
       CK(eng.gemm(P, b, b, b, one, Fc(K), OP_C, Fc(glb), OP_N, zero, F(Vtb), zero, none, nullptr));
       // Vt = g^<_{i-1} K^H
-      CK(eng.gemm(P, b, b, b, one, Fc(Vtb), OP_C, Fc(S(w.glF, i - 1)), OP_N, one, F(Kb), zero, none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(Vtb), OP_C, Fc(glF(i - 1)), OP_N, one, F(Kb), zero, none, nullptr));
       CK(eng.gemm(P, b, b, b, one, Fc(Vtb), OP_N, Fc(K), OP_N, one, F(S(w.glbar, i - 1)), zero, none,
                   nullptr));
       // K = g_i t_{i-1}^H
@@ -311,16 +420,16 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
     }
     if (has_src(i)) {
       CK(build_src(i, Ssrc));
-      CK(eng.gemm(P, b, b, b, one, Fc(S(w.gF, i)), OP_N, Fc(Ssrc), OP_N, zero, F(Wsrc), zero, none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(gF(i)), OP_N, Fc(Ssrc), OP_N, zero, F(Wsrc), zero, none, nullptr));
       // g^<_i += Wsrc g_i^H
-      CK(eng.gemm(P, b, b, b, one, Fc(glb), OP_N, Fc(S(w.gF, i)), OP_N, zero, F(Wbar), zero, none, nullptr));
+      CK(eng.gemm(P, b, b, b, one, Fc(glb), OP_N, Fc(gF(i)), OP_N, zero, F(Wbar), zero, none, nullptr));
       CK(eng.gemm(P, b, b, b, one, Fc(glb), OP_C, Fc(Wsrc), OP_N, one, F(gb), zero, none, nullptr));
       // Wsrc = g_i S
       CK(eng.gemm(P, b, b, b, one, Fc(Wbar), OP_N, Fc(Ssrc), OP_C, one, F(gb), zero, none, nullptr));
     }
     // g_i = M_i^-1:  Mbar = -g^H gbar g^H
-    CK(eng.gemm(P, b, b, b, one, Fc(gb), OP_N, Fc(S(w.gF, i)), OP_C, zero, F(T1), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, mone, Fc(S(w.gF, i)), OP_C, Fc(T1), OP_N, zero, F(Mb), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, one, Fc(gb), OP_N, Fc(gF(i)), OP_C, zero, F(T1), zero, none, nullptr));
+    CK(eng.gemm(P, b, b, b, mone, Fc(gF(i)), OP_C, Fc(T1), OP_N, zero, F(Mb), zero, none, nullptr));
     k_vbar<<<g2(b, P), kT, 0, s>>>(b, i, NB, Fc(Mb), w.vb);
     count_launch();
     if (i > 0) {
@@ -331,6 +440,7 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
                   F(S(w.gbar, i - 1)), zero, none, nullptr));
     }
   }
+#undef RUN
   k_sum_points<<<(NB + kT - 1) / kT, kT, 0, s>>>(P, NB, w.vb, a.Vbar, a.accumulate ? 1 : 0);
   count_launch();
   CK(cudaGetLastError());
@@ -345,7 +455,8 @@ constexpr size_t kAdjBudget = 32ull << 30;
 size_t adjoint_bytes(const negf_device* dev, int P, const negf_options* opt) {
   size_t off = 0;
   AdjWs w;
-  carve_adj(nullptr, off, P, dev->block, dev->n_slabs, opt->precision, w);
+  carve_adj(nullptr, off, P, dev->block, dev->n_slabs, adj_segment(opt, dev->n_slabs),
+            opt->precision, w);
   return off + 256;
 }
 
@@ -373,7 +484,8 @@ extern "C" negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, c
       (dev->n_slabs > 1 && !dev->H_up) || n_pts < 0)
     return NEGF_ERR_ARG;
   if (!engine_supports(opt->precision)) return NEGF_ERR_UNSUPPORTED;
-  if (!(opt->kT > 0.0) || opt->refine_steps < 0 || opt->refine_steps > 8 || opt->chunk < 0)
+  if (!(opt->kT > 0.0) || opt->refine_steps < 0 || opt->refine_steps > 8 || opt->chunk < 0 ||
+      opt->adjoint_segment < 0)
     return NEGF_ERR_ARG;
   if (!V_bar) return NEGF_ERR_ARG;
   const int b = dev->block, N = dev->n_slabs;

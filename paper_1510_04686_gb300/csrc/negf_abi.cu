@@ -48,7 +48,7 @@ bool valid_opt(const negf_options* o) {
   if (!(o->sr_tol > 0.0) || o->sr_max_iter < 1 || o->sr_max_iter > 100000) return false;
   if (o->precision != NEGF_PREC_FP64 && o->precision != NEGF_PREC_MIXED) return false;
   if (o->refine_steps < 0 || o->refine_steps > 8 || o->chunk < 0) return false;
-  if (o->sr_host_check < 0) return false;
+  if (o->sr_host_check < 0 || o->adjoint_segment < 0) return false;
   return true;
 }
 
@@ -394,7 +394,7 @@ void negf_default_options(negf_options* o) {
   o->refine_steps = 2;
   o->chunk = 0;
   o->sr_host_check = 4;
-  o->reserved = 0;
+  o->adjoint_segment = 0;
 }
 
 int32_t negf_abi_version(void) { return NEGF_ABI_VERSION; }

@@ -41,7 +41,7 @@ class _Opt(ctypes.Structure):
     _fields_ = [("eta_lead", c_double), ("eta_device", c_double), ("mu_L", c_double),
                 ("mu_R", c_double), ("kT", c_double), ("sr_tol", c_double),
                 ("sr_max_iter", c_int32), ("precision", c_int32), ("refine_steps", c_int32),
-                ("chunk", c_int32), ("sr_host_check", c_int32), ("reserved", c_int32)]
+                ("chunk", c_int32), ("sr_host_check", c_int32), ("adjoint_segment", c_int32)]
 
 
 _LIB = None
