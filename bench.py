@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--points-per-step", type=int, default=128)
+    ap.add_argument("--points-per-step", type=int, default=256)
     ap.add_argument("--cpu-points", type=int, default=2)
     ap.add_argument("--fp64-points", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true",
@@ -390,6 +390,7 @@ def main():
     n_launch, tc_ms, alg, hw = negf.profile_read(negf.PROF_TC_GEMM)
     sl_n, sl_ms, _, _ = negf.profile_read(negf.PROF_SLICE)
     inv_n, inv_ms, _, _ = negf.profile_read(negf.PROF_INV)
+    pan_n, pan_ms, _, _ = negf.profile_read(negf.PROF_GJ_PANEL)
     points = args.steps * P * world
     value = points / (ms / 1e3)
 
@@ -409,6 +410,7 @@ def main():
         "share_of_step": tc_ms / ms if ms > 0 else None,
         "slicing_share_of_step": sl_ms / ms if ms > 0 else None,
         "inverse_elimination_share_of_step": inv_ms / ms if ms > 0 else None,
+        "gj_panel_share_of_step": pan_ms / ms if ms > 0 else None,
         "traffic": (TC_DRAM_BYTES_PER_ITEM_B400 * (alg / max(n_launch, 1)) / (8.0 * WORK["b"] ** 3)
                     if TC_DRAM_BYTES_PER_ITEM_B400 and WORK["b"] == 400 and n_launch
                     and prec == negf.PREC_MIXED and negf.tc_config() == TC_PROFILED_CONFIG

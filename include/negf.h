@@ -279,7 +279,8 @@ int32_t negf_tc_config_get(void);
  * of kernels this library has launched since it was loaded.  With profiling on, every launch of
  * the tensor-core GEMM kernel (kind 0), of its operand slicing (kind 1) and every Gauss-Jordan
  * elimination of a block inverse inside the sweeps (kind 2: the FP32 start of the mixed form or
- * the whole FP64 inverse, without the Newton-Schulz products, which count as kinds 0 and 1) is
+ * the whole FP64 inverse, without the Newton-Schulz products, which count as kinds 0 and 1) and
+ * every launch of its panel-elimination kernel (kind 3, a part of kind 2) is
  * bracketed by CUDA events on its own stream; negf_profile_read synchronises those events and
  * returns the cumulative launches and milliseconds of the kind since the last
  * negf_profile_reset. */

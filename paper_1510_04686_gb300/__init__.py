@@ -27,6 +27,7 @@ from .negf import (  # noqa: F401
     rgf,
     PROF_SLICE,
     PROF_INV,
+    PROF_GJ_PANEL,
     workspace_size,
     library,
     PREC_FP64,

@@ -242,10 +242,17 @@ __global__ void __launch_bounds__(kThreads) k_gj_panel(int n, int k0, int w, int
       for (int u = 0; u < 8; ++u)
         if (j0 + u < w) Tp[(long long)(j0 + u) * n + c] = v[u];
     }
-    // (2) rows below the panel that took part in a swap receive a panel row's content
-    for (int jj = 0; jj < w; ++jj) {
-      const int r = spv[jj];
-      if (r >= k0 + w) a[(long long)r * ld + c] = a[(long long)cont[r] * ld + c];
+    // (2) rows below the panel that took part in a swap receive a panel row's content (all
+    // sources are panel rows, read before any is cleared; loads batched ahead of the stores)
+    for (int j0 = 0; j0 < w; j0 += 8) {
+      cx<R> v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < w && spv[j0 + u] >= k0 + w)
+          v[u] = a[(long long)cont[spv[j0 + u]] * ld + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < w && spv[j0 + u] >= k0 + w) a[(long long)spv[j0 + u] * ld + c] = v[u];
     }
     // (3) the pivot rows are cleared outside the panel
     for (int jj = 0; jj < w; ++jj) a[(long long)(k0 + jj) * ld + c] = zero;
@@ -299,6 +306,7 @@ static size_t panel_smem(int n, int w, int elem_bytes) {
 
 bool gj_fits_small(int n, int elem_bytes) { return small_smem(n, elem_bytes) <= kSmemBudget; }
 
+
 int gj_panel_width(int n, int elem_bytes) {
   size_t per_col = (size_t)n * elem_bytes + elem_bytes + sizeof(int);
   size_t fixed = (size_t)n * (elem_bytes + sizeof(int));
@@ -329,7 +337,9 @@ cudaError_t gj_inverse(cudaStream_t s, int P, int n, BM<R> M, BM<R> X, cx<R>* U,
   for (int k0 = 0; k0 < n; k0 += nb) {
     const int w = std::min(nb, n - k0);
     size_t smem = panel_smem(n, w, eb);
+    prof_begin(s, PROF_GJ_PANEL);
     k_gj_panel<R><<<P, kThreads, smem, s>>>(n, k0, w, nb, M, U, T, piv, status, active);
+    prof_end(s, PROF_GJ_PANEL);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     BMc<R> Ua{U, (long long)n * nb, nullptr, nb};

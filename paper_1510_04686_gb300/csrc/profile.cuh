@@ -13,5 +13,5 @@ void prof_begin(cudaStream_t s, int kind);
 void prof_end(cudaStream_t s, int kind);
 // Add the flops one launch dispatches: complex algorithmic 8 M N K and issued BF16 MMA flops.
 void prof_flops(int kind, double alg, double hw);
-enum { PROF_TC_GEMM = 0, PROF_SLICE = 1, PROF_INV = 2, PROF_KINDS = 3 };
+enum { PROF_TC_GEMM = 0, PROF_SLICE = 1, PROF_INV = 2, PROF_GJ_PANEL = 3, PROF_KINDS = 4 };
 }  // namespace negf

@@ -363,7 +363,7 @@ def zinv(M, precision=PREC_FP64, refine_steps=2):
     return X, st
 
 
-PROF_TC_GEMM, PROF_SLICE, PROF_INV = 0, 1, 2
+PROF_TC_GEMM, PROF_SLICE, PROF_INV, PROF_GJ_PANEL = 0, 1, 2, 3
 
 
 def profile(enable: bool):

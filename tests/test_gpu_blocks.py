@@ -103,6 +103,31 @@ def test_zinv_matches_numpy(prec, steps, n):
         assert err < 1e-15 * kappa * n, (p, err, kappa)
 
 
+@pytest.mark.parametrize("prec,steps", [(0, 0), (1, 2)])
+@pytest.mark.parametrize("n", [200, 400])
+def test_zinv_large_batch(prec, steps, n):
+    """A batch of 100 matrices at the sweep's sizes (panel Gauss-Jordan with batched trailing
+    updates, FP64 and FP32 + Newton-Schulz); same accuracy bar as the small batches."""
+    rng = np.random.default_rng(n + 1)
+    nb = 100
+    H = _rand(rng, (nb, n, n), 1.0 / np.sqrt(n))
+    H = 0.5 * (H + np.swapaxes(H, 1, 2).conj())
+    z = (np.linspace(-1.5, 1.5, nb) + 1j * np.geomspace(1e-6, 1e-2, nb))
+    M = z[:, None, None] * np.eye(n) - H
+    X, st = negf.zinv(torch.as_tensor(M.copy(), device="cuda"), precision=prec,
+                      refine_steps=steps)
+    X = X.cpu().numpy()
+    assert np.all(st.cpu().numpy() == 0)
+    ref = np.linalg.inv(M)
+    for p in range(0, nb, 7):
+        kappa = np.linalg.norm(M[p], 2) * np.linalg.norm(ref[p], 2)
+        err = np.abs(X[p] - ref[p]).max() / np.abs(ref[p]).max()
+        assert err < 1e-15 * kappa * n, (p, err, kappa)
+    # every item: residual of the inverse
+    R = np.einsum("pij,pjk->pik", M, X) - np.eye(n)
+    assert np.all(np.isfinite(X)) and np.abs(R).max() < 1e-6
+
+
 def test_zinv_reports_singular():
     M = torch.zeros((2, 8, 8), dtype=torch.complex128, device="cuda")
     M[0] = torch.eye(8, dtype=torch.complex128, device="cuda")

@@ -2,7 +2,7 @@
 
 The device is the benchmark's: N = 70 slabs x 400 x 400 blocks (40 atoms x 10 orbitals), Si with
 p(Ge) = 0.1, transverse k-points with k-independent hoppings, eta = 1e-6 in leads and device.
-A batch of 128 (E, k) points is solved in one chunk (the bench's points per step) in the mixed
+A batch of 256 (E, k) points is solved in one chunk (the bench's points per step) in the mixed
 form; two points of the batch, and a 4-point FP64 batch, are checked element by element against
 the CPU oracle, which solves them one by one.
 
@@ -27,7 +27,7 @@ negf = pytest.importorskip("paper_1510_04686_gb300")
 pytestmark = pytest.mark.gpu
 
 N, B, N_E, N_K, SEED = 70, 400, 512, 8, 1001
-P = 128          # points per launch chain, as in bench.py
+P = 256          # points per launch chain, as in bench.py
 SAMPLED = (17, 90)
 
 
