@@ -137,8 +137,9 @@ cudaError_t Engine::inv(int P, BM<double> Mm, BM<double> X, int32_t* status,
                 mkc(0.0, 0.0), none, true, active, tw);
     if (e != cudaSuccess) return e;
     BM<double> Xn{nxt, bb, nullptr, b};
+    // X + X R with |R| << 1: only accuracy relative to |X| matters for the correction
     e = tc_gemm(s, P, b, b, b, mkc(1.0, 0.0), Xc, OP_N, cst(R), OP_N, mkc(0.0, 0.0), Xn,
-                mkc(1.0, 0.0), Xc, false, active, tw);
+                mkc(1.0, 0.0), Xc, false, active, tw, 0, true);
     if (e != cudaSuccess) return e;
     std::swap(cur, nxt);
   }

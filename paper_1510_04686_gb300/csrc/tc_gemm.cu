@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int32_t* __restrict__ zidxA, int zmodeA, const int32_t* __restrict__ zidxB,
               int zmodeB, z64 alpha,
               z64 beta, z64 gamma, BM<double> C, BMc<double> D, int add_identity,
-              const int32_t* active, int32_t* err) {
+              int trunc_beta, const int32_t* active, int32_t* err) {
   static_assert(NT * (kAccBufs + 2) == 512, "TMEM: kAccBufs accumulators + hi / lo sum words");
   static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair per MMA");
   using CF = Cfg<NT, STAGES, CG, G>;
@@ -482,6 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* accempty = accfull + kAccBufs;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accempty + kAccBufs);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* s_cut = reinterpret_cast<int*>(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * NT;  // pairs are adjacent along x
@@ -499,6 +500,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&accempty[i], CG * kEpiWarps);  // one arrival per epilogue warp of the pair
     }
     *abort_flag = 0;
+    // Highest slice order this tile computes.  With trunc_beta > 0 the product only has to be
+    // accurate relative to |op(A)| rows (it is a small correction added to a term of that size):
+    // orders whose terms fall below 2^(-beta S) of the A row scale are dropped, from the largest
+    // column exponent f of op(B) over the tile (|B| < 2^f): keep d <= S + ceil(f / beta).
+    int cut = S;
+    if (trunc_beta > 0) {
+      const int Nc = N2 >> 1;
+      int fmax = -(1 << 30);
+      for (int n = n0 / 2; n < min(Nc, n0 / 2 + NT / 2); ++n)
+        fmax = max(fmax, fB[(long long)zB * Nc + n]);
+      if (fmax < 0) cut = max(1, S - (-fmax) / trunc_beta);
+    }
+    *s_cut = cut;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 9) {
@@ -519,6 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if constexpr (CG == 2) cluster_sync();  // the peer's barriers exist before any remote use
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const int cut = *s_cut;
 
   if (warp == 8) {
     // ---------------- TMA producer: for every item, the K chunks of its part
@@ -527,6 +542,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       for (int ii = 0; ii < sched.n_items && !*abort_flag; ++ii) {
         const Item it = sched.it[ii];
+        if (it.s + it.t - 1 > cut) continue;
         for (int kc = sched.part_lo[it.kp]; kc < sched.part_hi[it.kp]; ++kc) {
           // a group of G stages is released by one MMA commit: wait at the group's first stage
           if (stage % G == 0 && !mbar_wait(&empty[stage / G], phase ^ 1, abort_flag)) break;
@@ -572,16 +588,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc = idesc_bf16(kBM * CG, NT);
       int stage = 0;
       uint32_t phase = 0;
-      int cur = -1;
+      int cur = -1, gexec = -1, buf = 0;  // gexec: accumulator groups computed so far
       uint32_t acc_on = 0;
       for (int ii = 0; ii < sched.n_items && !*abort_flag; ++ii) {
         const Item it = sched.it[ii];
-        const int buf = it.acc % kAccBufs;
+        if (it.s + it.t - 1 > cut) continue;
         if (it.acc != cur) {
           cur = it.acc;
+          ++gexec;
+          buf = gexec % kAccBufs;
           acc_on = 0;
-          if (cur >= kAccBufs) {  // the buffer's previous group must have been read out
-            if (!mbar_wait(&accempty[buf], ((cur / kAccBufs) - 1) & 1, abort_flag)) break;
+          if (gexec >= kAccBufs) {  // the buffer's previous group must have been read out
+            if (!mbar_wait(&accempty[buf], ((gexec / kAccBufs) - 1) & 1, abort_flag)) break;
             tc_fence_after();
           }
         }
@@ -616,7 +634,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (!ok) break;
-        const bool last_of_acc = (ii + 1 == sched.n_items) || (sched.it[ii + 1].acc != cur);
+        int nx = ii + 1;  // next item that is computed
+        while (nx < sched.n_items && sched.it[nx].s + sched.it[nx].t - 1 > cut) ++nx;
+        const bool last_of_acc = (nx == sched.n_items) || (sched.it[nx].acc != cur);
         if (last_of_acc) {
           if constexpr (CG == 2)
             mma_commit_pair(&accfull[buf]);
@@ -650,11 +670,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int cbase = half * (NT / 2);
     const uint32_t t_hi = tmem + lane_off + kAccBufs * NT, t_lo = t_hi + NT;
-    for (int acc = 0; acc < sched.n_acc; ++acc) {
+    const int n_exec = (sched.n_acc / S) * min(cut, S);  // groups of orders <= cut per part
+    for (int acc = 0; acc < n_exec; ++acc) {
       const int buf = acc % kAccBufs;
       if (!mbar_wait(&accfull[buf], (acc / kAccBufs) & 1, abort_flag)) break;
       tc_fence_after();
-      const bool last = (acc == sched.n_acc - 1);
+      const bool last = (acc == n_exec - 1);
       for (int c0 = cbase; c0 < cbase + NT / 2; c0 += 32) {
         uint32_t v[32], h[32], l[32];
         tmem_ld32(tmem + lane_off + (uint32_t)(buf * NT + c0), v);
@@ -810,7 +831,7 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
                       int n_parts, const CUtensorMap& mA, const CUtensorMap& mB, const TcWs& ws,
                       const int32_t* zA, int zmA, const int32_t* zB, int zmB, z64 alpha,
                       z64 beta, z64 gamma, BM<double> C, BMc<double> D, bool add_identity,
-                      const int32_t* active) {
+                      int trunc_beta, const int32_t* active) {
   using CF = Cfg<NT, STAGES, CG, G>;
   static bool attr = false;
   if (!attr) {
@@ -847,7 +868,7 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
   cudaError_t e = cudaLaunchKernelEx(&lc, k_tc_gemm<NT, STAGES, CG, G>, mA, mB, sc, M, N2, S,
                                      two_beta, (const int32_t*)ws.expA, (const int32_t*)ws.expB,
                                      zA, zmA, zB, zmB, alpha, beta, gamma, C, D,
-                                     add_identity ? 1 : 0, active, ws.err);
+                                     add_identity ? 1 : 0, trunc_beta, active, ws.err);
   prof_end(s, PROF_TC_GEMM);
   count_launch();
   if (e != cudaSuccess) return e;
@@ -972,7 +993,7 @@ void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, TcWs& w) {
 cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<double> A,
                     int opA, BMc<double> B, int opB, z64 beta, BM<double> C, z64 gamma,
                     BMc<double> D, bool add_identity, const int32_t* active, const TcWs& ws,
-                    int n_distinct) {
+                    int n_distinct, bool trunc_a) {
   if (P <= 0 || M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   // Operands shared by all items (stride 0) or selected per item from n_distinct matrices are
   // sliced once per distinct matrix; the kernel maps each item to its slice set.
@@ -1021,7 +1042,7 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
   if (!make_map(&mB, sb, L, N2, (long long)PB * S, kNT / CG)) return cudaErrorInvalidValue;
 #define NEGF_TC_ARGS                                                                          \
   s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB, zmB, alpha, beta, gamma, C, D, \
-      add_identity, active
+      add_identity, trunc_a ? bta : 0, active
   switch (cfg / 2) {
     case 0: return launch_tc<kNT, 6, 1, 1>(NEGF_TC_ARGS);
     case 1: return launch_tc<kNT, 6, 1, 2>(NEGF_TC_ARGS);

@@ -40,10 +40,14 @@ cudaError_t tc_timeout_reset(cudaStream_t s, const TcWs& ws);
 cudaError_t tc_timeout_flag(cudaStream_t s, const TcWs& ws, int P, int32_t* status);
 
 // n_distinct: number of different matrices an indexed operand (idx != NULL) selects from
-// (0 = unknown: slice every item).
+// (0 = unknown: slice every item).  trunc_a: the product only needs to be accurate relative
+// to the rows of op(A) (it is a correction much smaller than a term of that size, such as
+// X R in the Newton-Schulz step X + X R with |R| < 1): each output tile drops the slice orders
+// whose terms stay below 2^(-beta S) of the A row scale, given the largest column exponent of
+// op(B) in the tile.  The issued-flop count of the launch is then an upper bound.
 cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<double> A,
                     int opA, BMc<double> B, int opB, z64 beta, BM<double> C, z64 gamma,
                     BMc<double> D, bool add_identity, const int32_t* active, const TcWs& ws,
-                    int n_distinct = 0);
+                    int n_distinct = 0, bool trunc_a = false);
 
 }  // namespace negf
