@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--scba-energies", type=int, default=128)
     ap.add_argument("--adj-slabs", type=int, default=20)
     ap.add_argument("--ragged-points", type=int, default=16)
+    ap.add_argument("--tc-config", type=int, default=None,
+                    help="tensor-core GEMM configuration (default: autotuned per block size "
+                         "and batch for the rgf workload, the library default otherwise)")
     ap.add_argument("--gemm-b", type=int, default=400)
     ap.add_argument("--gemm-batch", type=int, default=64)
     return ap.parse_args()
@@ -261,6 +264,8 @@ def run_side(args):
                                         " V ~ U(-0.3, 0.3) eV per atom, 1 point"})
     elif args.workload == "gemm":
         b, nb = args.gemm_b, args.gemm_batch
+        if args.tc_config is not None:
+            negf.tc_config(args.tc_config)
         g = torch.Generator(device=dvc).manual_seed(1)
         A = torch.randn((nb, b, b), dtype=torch.complex128, device=dvc, generator=g)
         B = torch.randn((nb, b, b), dtype=torch.complex128, device=dvc, generator=g)
@@ -330,9 +335,12 @@ def main():
     P = args.points_per_step
     tuned = None
     if prec == negf.PREC_MIXED:
-        # pick the tensor-core GEMM configuration for this block size and batch (untimed)
-        from paper_1510_04686_gb300 import autotune
-        tuned = autotune.tune_tc(WORK["b"], P)["config"]
+        if args.tc_config is not None:
+            tuned = negf.tc_config(args.tc_config)
+        else:
+            # pick the tensor-core GEMM configuration for this block size and batch (untimed)
+            from paper_1510_04686_gb300 import autotune
+            tuned = autotune.tune_tc(WORK["b"], P)["config"]
     opt = negf.options(precision=prec, chunk=P)
     n_tot = WORK["n_E"] * WORK["n_k"]
     total_steps = args.warmup + args.steps

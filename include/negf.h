@@ -264,11 +264,15 @@ negf_status negf_zinv_batched_noalloc(int32_t n_batch, int32_t n, double* M, dou
 /* ---- tensor-core GEMM configuration (autotuning) ----------------------------------------
  * The mixed-precision GEMM has negf_tc_config_count() kernel configurations, differing only in
  * speed: configuration c uses the kernel shape c / 2 of
- *   (6 stages, 1 CTA, 1), (6, 1, 2), (6, 1, 3), (8 stages, CTA pair, 1), (8, 2, 2), (8, 2, 4)
+ *   (6 stages, 1 CTA, 1), (6, 1, 2), (6, 1, 3), (8 stages, CTA pair, 1), (8, 2, 2), (8, 2, 4),
+ *   (6, 1, 1, windowed), (3, 1, 1, 2 K chunks per stage), (4, 2, 1, 2 K chunks per stage),
+ *   (2, 1, 1, 3 K chunks per stage), (2, 2, 1, 4 K chunks per stage)
  * = (shared-memory pipeline stages, CTAs per MMA: one 128-row tile or a pair of CTAs with a
- * 256-row MMA, stages released per MMA commit) and splits K into at most (4, 8)[c % 2] exactly
- * accumulated parts (more parts allow wider slices and fewer slice products).
- * negf_tc_config_set selects one process-wide (default 0); results agree to the GEMM's
+ * 256-row MMA, stages released per MMA commit; windowed: slice orders taken two at a time so
+ * that each loaded B slice tile serves two products; K chunks of 64 per stage) and splits K
+ * into at most (4, 8)[c % 2] exactly accumulated parts (more parts allow wider slices and fewer
+ * slice products).
+ * negf_tc_config_set selects one process-wide (default 18); results agree to the GEMM's
  * rounding.  The package's autotuner times them per block size and stores the choice. */
 int32_t negf_tc_config_count(void);
 negf_status negf_tc_config_set(int32_t idx);

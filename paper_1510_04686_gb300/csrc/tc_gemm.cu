@@ -30,12 +30,18 @@ constexpr int kMaxParts = 8;
 struct Item {
   int8_t acc, s, t, kp;  // accumulator group, A slice, B slice, K part
 };
+constexpr int kMaxWin = 16;
 struct Sched {
   int n_items;
   int n_acc;
   int part_lo[kMaxParts];  // first K chunk of each part
   int part_hi[kMaxParts];  // one past the last K chunk
   Item it[kMaxItems];
+  // windowed schedule: per part, windows of one order d or of two orders (d, d + 1)
+  int n_parts;
+  int n_win;
+  int8_t win_d[kMaxWin];
+  int8_t win_pair[kMaxWin];
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -398,14 +404,16 @@ __global__ void __launch_bounds__(256) k_slice(int n_lines, int K, int L, BMc<do
 // A and one half of the B tile (NT / 2 rows of the embedded B), so a stage moves 24 KB per CTA
 // instead of 32 KB, and each CTA's tensor memory receives the accumulator of its own rows.  Both
 // CTAs' loads complete on the even CTA's barrier; the MMA commits arrive on both CTAs' barriers.
-template <int NT, int STAGES, int CG, int G>
+template <int NT, int STAGES, int CG, int G, int KPS = 1>
 struct Cfg {
   static_assert(STAGES % G == 0, "stages are released in whole groups");
   static constexpr int kStages = STAGES;
   static constexpr int kGroups = STAGES / G;                  // stage groups (one commit each)
-  static constexpr int kATile = kBM * kKC * 2;                // 16 KB
   static constexpr int kBRows = NT / CG;                      // rows of the B tile this CTA loads
-  static constexpr int kBTile = kBRows * kKC * 2;
+  static constexpr int kABox = kBM * kKC * 2;                 // one K chunk of A: 16 KB
+  static constexpr int kBBox = kBRows * kKC * 2;              // one K chunk of B
+  static constexpr int kATile = KPS * kABox;                  // a stage holds KPS K chunks
+  static constexpr int kBTile = KPS * kBBox;
   static constexpr int kStage = kATile + kBTile;
   static constexpr int kStagingPerWarp = 32 * 8 * 16;         // 32 rows x 8 complex outputs
   static constexpr int kStaging = kEpiWarps * kStagingPerWarp;
@@ -456,7 +464,17 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
                : "memory");
 }
 
-template <int NT, int STAGES, int CG, int G>
+// WIN: windowed schedule (CG = 1, G = 1).  The slice orders of a part are taken in windows of
+// one order {d} or two orders {d, d + 1}; a window walks its A slices s = 1, 2, ... and each
+// shared-memory stage holds (A_s, B_{d+1-s}).  A step issues A_s x B_{d+1-s} into order d and
+// A_s x B_{d+2-s} (the previous stage's B tile, still resident) into order d + 1, so one B tile
+// serves two products: for S = 7 a K chunk moves 32 tiles instead of 56 for the same 28
+// products.  A stage whose B tile the next step reuses is released one step later; the two
+// accumulators of a pair window are both live, so the MMAs wait for the epilogue between
+// windows.
+// KPS: K chunks (of 64 BF16 columns) per shared-memory stage; more chunks per stage put more
+// MMAs behind each barrier wait and commit of the MMA thread.
+template <int NT, int STAGES, int CG, int G, bool WIN, int KPS = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const Sched sched, int M, int N2, int S, int two_beta,
@@ -467,7 +485,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               int trunc_beta, const int32_t* active, int32_t* err) {
   static_assert(NT * (kAccBufs + 2) == 512, "TMEM: kAccBufs accumulators + hi / lo sum words");
   static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair per MMA");
-  using CF = Cfg<NT, STAGES, CG, G>;
+  static_assert(!WIN || (CG == 1 && G == 1), "windowed schedule: one CTA, one stage per commit");
+  using CF = Cfg<NT, STAGES, CG, G, KPS>;
+  static_assert(!WIN || KPS == 1, "windowed schedule: one K chunk per stage");
   constexpr int kStages = CF::kStages;
   const int p = blockIdx.z;
   // both CTAs of a pair have the same item, so they leave together (before any cluster barrier)
@@ -535,7 +555,125 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_slot;
   const int cut = *s_cut;
 
-  if (warp == 8) {
+  if (WIN && warp == 8) {
+    // ---------------- TMA producer, windowed schedule
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int q = 0; q < sched.n_parts && ok; ++q)
+        for (int w = 0; w < sched.n_win && ok; ++w) {
+          const int d = sched.win_d[w];
+          const bool pair = sched.win_pair[w] != 0;
+          const int nsteps = pair ? d + 2 : d;
+          for (int kc = sched.part_lo[q]; kc < sched.part_hi[q] && ok; ++kc)
+            for (int st = 0; st < nsteps; ++st) {
+              // pair: step 0 loads B_{d+1}; step s loads (A_s, B_{d+1-s}); step d+1 loads A_{d+1}
+              // single order: step st loads (A_{st+1}, B_{d-st})
+              const int a = pair ? st : st + 1;
+              const int bs = pair ? (st <= d ? d + 1 - st : 0) : d - st;
+              if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
+                ok = false;
+                break;
+              }
+              unsigned char* stp = smem + stage * CF::kStage;
+              mbar_expect_tx(&full[stage], (a ? CF::kATile : 0) + (bs ? CF::kBTile : 0));
+              if (a) tma_load_3d(stp, &mapA, &full[stage], kc * kKC, m0, zA * S + a - 1);
+              if (bs)
+                tma_load_3d(stp + CF::kATile, &mapB, &full[stage], kc * kKC, n0, zB * S + bs - 1);
+              if (++stage == kStages) {
+                stage = 0;
+                phase ^= 1;
+              }
+            }
+        }
+      for (int i = 0; i < kStages; ++i) {  // drain: every stage is released by the MMAs
+        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
+        if (++stage == kStages) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+  } else if (WIN && warp == 9) {
+    // ---------------- MMA issuer, windowed schedule
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kBM, NT);
+      int stage = 0;
+      uint32_t phase = 0;
+      int held = -1;  // stage whose B tile the current step still reads
+      uint32_t acc_on[2] = {0, 0};
+      bool ok = true;
+      auto start_group = [&](int g) -> bool {
+        if (g >= 2) {
+          if (!mbar_wait(&accempty[g & 1], ((g >> 1) - 1) & 1, abort_flag)) return false;
+          tc_fence_after();
+        }
+        acc_on[g & 1] = 0;
+        return true;
+      };
+      auto product = [&](int g, uint32_t a_addr, uint32_t b_addr) {
+        const uint32_t dcol = tmem + (uint32_t)((g & 1) * NT);
+#pragma unroll
+        for (int k = 0; k < kKC / 16; ++k) {
+          mma_bf16(dcol, sw128_desc(a_addr + 32 * k), sw128_desc(b_addr + 32 * k), idesc,
+                   acc_on[g & 1]);
+          acc_on[g & 1] = 1;
+        }
+      };
+      for (int q = 0; q < sched.n_parts && ok; ++q)
+        for (int w = 0; w < sched.n_win && ok; ++w) {
+          const int d = sched.win_d[w];
+          const bool pair = sched.win_pair[w] != 0;
+          const int nsteps = pair ? d + 2 : d;
+          const int gA = q * S + d - 1;  // group of order d (order d + 1: gA + 1)
+          for (int kc = sched.part_lo[q]; kc < sched.part_hi[q] && ok; ++kc) {
+            const bool first = (kc == sched.part_lo[q]), lastk = (kc == sched.part_hi[q] - 1);
+            for (int st = 0; st < nsteps; ++st) {
+              if (!mbar_wait(&full[stage], phase, abort_flag)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t a0 = smem_u32(smem + stage * CF::kStage);
+              if (pair) {
+                if (st >= 1 && st <= d) {  // A_s x B_{d+1-s} (this stage) into order d
+                  if (first && st == 1 && !(ok = start_group(gA))) break;
+                  product(gA, a0, a0 + CF::kATile);
+                }
+                if (st >= 1) {  // A_s x B_{d+2-s} (previous stage) into order d + 1
+                  if (first && st == 1 && !(ok = start_group(gA + 1))) break;
+                  product(gA + 1, a0, smem_u32(smem + held * CF::kStage) + CF::kATile);
+                }
+              } else {
+                if (first && st == 0 && !(ok = start_group(gA))) break;
+                product(gA, a0, a0 + CF::kATile);
+              }
+              if (held >= 0) {  // the previous stage's B tile has served its second product
+                mma_commit(&empty[held]);
+                held = -1;
+              }
+              if (pair && st <= d)
+                held = stage;  // the next step reads this stage's B tile
+              else
+                mma_commit(&empty[stage]);
+              if (lastk) {
+                if (pair) {
+                  if (st == d) mma_commit(&accfull[gA & 1]);
+                  if (st == d + 1) mma_commit(&accfull[(gA + 1) & 1]);
+                } else if (st == d - 1) {
+                  mma_commit(&accfull[gA & 1]);
+                }
+              }
+              if (++stage == kStages) {
+                stage = 0;
+                phase ^= 1;
+              }
+            }
+          }
+        }
+    }
+  } else if (warp == 8) {
     // ---------------- TMA producer: for every item, the K chunks of its part
     if (lane == 0) {
       int stage = 0;
@@ -543,21 +681,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int ii = 0; ii < sched.n_items && !*abort_flag; ++ii) {
         const Item it = sched.it[ii];
         if (it.s + it.t - 1 > cut) continue;
-        for (int kc = sched.part_lo[it.kp]; kc < sched.part_hi[it.kp]; ++kc) {
+        const int hi = sched.part_hi[it.kp];
+        for (int kc = sched.part_lo[it.kp]; kc < hi; kc += KPS) {
           // a group of G stages is released by one MMA commit: wait at the group's first stage
           if (stage % G == 0 && !mbar_wait(&empty[stage / G], phase ^ 1, abort_flag)) break;
           unsigned char* st = smem + stage * CF::kStage;
+          const int nch = min(KPS, hi - kc);  // K chunks in this stage
           if constexpr (CG == 2) {
             // both CTAs' loads of this stage complete on the even CTA's barrier
-            if (leader) mbar_expect_tx(&full[stage], CG * CF::kStage);
+            if (leader) mbar_expect_tx(&full[stage], CG * nch * (CF::kABox + CF::kBBox));
             const uint32_t fb = map_rank(smem_u32(&full[stage]), 0);
-            tma_load_3d_pair(st, &mapA, fb, kc * kKC, m0, zA * S + it.s - 1);
-            tma_load_3d_pair(st + CF::kATile, &mapB, fb, kc * kKC, n0 + (int)rank * CF::kBRows,
-                             zB * S + it.t - 1);
+#pragma unroll
+            for (int j = 0; j < KPS; ++j)
+              if (j < nch) {
+                tma_load_3d_pair(st + j * CF::kABox, &mapA, fb, (kc + j) * kKC, m0,
+                                 zA * S + it.s - 1);
+                tma_load_3d_pair(st + CF::kATile + j * CF::kBBox, &mapB, fb, (kc + j) * kKC,
+                                 n0 + (int)rank * CF::kBRows, zB * S + it.t - 1);
+              }
           } else {
-            mbar_expect_tx(&full[stage], CF::kStage);
-            tma_load_3d(st, &mapA, &full[stage], kc * kKC, m0, zA * S + it.s - 1);
-            tma_load_3d(st + CF::kATile, &mapB, &full[stage], kc * kKC, n0, zB * S + it.t - 1);
+            mbar_expect_tx(&full[stage], nch * (CF::kABox + CF::kBBox));
+#pragma unroll
+            for (int j = 0; j < KPS; ++j)
+              if (j < nch) {
+                tma_load_3d(st + j * CF::kABox, &mapA, &full[stage], (kc + j) * kKC, m0,
+                            zA * S + it.s - 1);
+                tma_load_3d(st + CF::kATile + j * CF::kBBox, &mapB, &full[stage], (kc + j) * kKC,
+                            n0, zB * S + it.t - 1);
+              }
           }
           if (++stage == kStages) {
             stage = 0;
@@ -605,22 +756,28 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         const uint32_t dcol = tmem + (uint32_t)(buf * NT);
         bool ok = true;
-        for (int kc = sched.part_lo[it.kp]; kc < sched.part_hi[it.kp]; ++kc) {
+        const int hi = sched.part_hi[it.kp];
+        for (int kc = sched.part_lo[it.kp]; kc < hi; kc += KPS) {
           if (!mbar_wait(&full[stage], phase, abort_flag)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t a0 = smem_u32(smem + stage * CF::kStage);
+          const int nch = min(KPS, hi - kc);
 #pragma unroll
-          for (int k = 0; k < kKC / 16; ++k) {
-            if constexpr (CG == 2)
-              mma_bf16_pair(dcol, sw128_desc(a0 + 32 * k), sw128_desc(a0 + CF::kATile + 32 * k),
-                            idesc, acc_on);
-            else
-              mma_bf16(dcol, sw128_desc(a0 + 32 * k), sw128_desc(a0 + CF::kATile + 32 * k), idesc,
-                       acc_on);
-            acc_on = 1;
+          for (int j = 0; j < KPS; ++j) {
+            if (j >= nch) break;
+            const uint32_t aj = a0 + j * CF::kABox, bj = a0 + CF::kATile + j * CF::kBBox;
+#pragma unroll
+            for (int k = 0; k < kKC / 16; ++k) {
+              if constexpr (CG == 2)
+                mma_bf16_pair(dcol, sw128_desc(aj + 32 * k), sw128_desc(bj + 32 * k), idesc,
+                              acc_on);
+              else
+                mma_bf16(dcol, sw128_desc(aj + 32 * k), sw128_desc(bj + 32 * k), idesc, acc_on);
+              acc_on = 1;
+            }
           }
           if (stage % G == G - 1) {  // last stage of its group: release the group
             if constexpr (CG == 2)
@@ -823,19 +980,29 @@ Sched build_sched(int S, int n_chunks, int n_parts) {
         sc.it[n++] = Item{(int8_t)g, (int8_t)s, (int8_t)(d + 1 - s), (int8_t)q};
   sc.n_items = n;
   sc.n_acc = g;
+  sc.n_parts = n_parts;
+  // windows {1}, {2, 3}, {4, 5}, ... (a last single order when S is even)
+  int w = 0;
+  sc.win_d[w] = 1;
+  sc.win_pair[w++] = 0;
+  for (int d = 2; d <= S && w < kMaxWin; d += 2) {
+    sc.win_d[w] = (int8_t)d;
+    sc.win_pair[w++] = (int8_t)(d + 1 <= S ? 1 : 0);
+  }
+  sc.n_win = w;
   return sc;
 }
 
-template <int NT, int STAGES, int CG, int G>
+template <int NT, int STAGES, int CG, int G, bool WIN = false, int KPS = 1>
 cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S, int two_beta,
                       int n_parts, const CUtensorMap& mA, const CUtensorMap& mB, const TcWs& ws,
                       const int32_t* zA, int zmA, const int32_t* zB, int zmB, z64 alpha,
                       z64 beta, z64 gamma, BM<double> C, BMc<double> D, bool add_identity,
                       int trunc_beta, const int32_t* active) {
-  using CF = Cfg<NT, STAGES, CG, G>;
+  using CF = Cfg<NT, STAGES, CG, G, KPS>;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NT, STAGES, CG, G>,
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NT, STAGES, CG, G, WIN, KPS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, CF::kSmem);
     if (e != cudaSuccess) return e;
     attr = true;
@@ -865,7 +1032,7 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
   at[0].val.clusterDim.z = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&lc, k_tc_gemm<NT, STAGES, CG, G>, mA, mB, sc, M, N2, S,
+  cudaError_t e = cudaLaunchKernelEx(&lc, k_tc_gemm<NT, STAGES, CG, G, WIN, KPS>, mA, mB, sc, M, N2, S,
                                      two_beta, (const int32_t*)ws.expA, (const int32_t*)ws.expB,
                                      zA, zmA, zB, zmB, alpha, beta, gamma, C, D,
                                      add_identity ? 1 : 0, trunc_beta, active, ws.err);
@@ -884,9 +1051,13 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
 struct TcShape {
   int stages, cg, grp;
 };
-constexpr TcShape kShapes[] = {{6, 1, 1}, {6, 1, 2}, {6, 1, 3}, {8, 2, 1}, {8, 2, 2}, {8, 2, 4}};
+constexpr TcShape kShapes[] = {{6, 1, 1}, {6, 1, 2}, {6, 1, 3}, {8, 2, 1}, {8, 2, 2}, {8, 2, 4},
+                               {6, 1, 1}, {3, 1, 1}, {4, 2, 1}, {2, 1, 1}, {2, 2, 1}};
+constexpr int kWindowedShape = 6;  // shape 6: (6, 1, 1) with the windowed schedule
+// shapes 7-10: several K chunks per stage: 2 (3 stages of 64 KB; a CTA pair: 4 stages of
+// 48 KB), 3 (2 stages of 96 KB), 4 (a CTA pair: 2 stages of 96 KB)
 constexpr int kNumCfg = 2 * (int)(sizeof(kShapes) / sizeof(kShapes[0]));
-std::atomic<int> g_cfg{0};
+std::atomic<int> g_cfg{18};
 
 void tc_plan(int K, int* beta, int* S, int* parts, int max_parts) {
   // Slices of beta bits, S = ceil(48 / beta), and the number of K parts such that every group
@@ -1043,13 +1214,20 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
 #define NEGF_TC_ARGS                                                                          \
   s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB, zmB, alpha, beta, gamma, C, D, \
       add_identity, trunc_a ? bta : 0, active
+  // the windowed schedule does not skip slice orders: truncated products take the plain one
+  if (cfg / 2 == kWindowedShape && !trunc_a) return launch_tc<kNT, 6, 1, 1, true>(NEGF_TC_ARGS);
   switch (cfg / 2) {
     case 0: return launch_tc<kNT, 6, 1, 1>(NEGF_TC_ARGS);
     case 1: return launch_tc<kNT, 6, 1, 2>(NEGF_TC_ARGS);
     case 2: return launch_tc<kNT, 6, 1, 3>(NEGF_TC_ARGS);
     case 3: return launch_tc<kNT, 8, 2, 1>(NEGF_TC_ARGS);
     case 4: return launch_tc<kNT, 8, 2, 2>(NEGF_TC_ARGS);
-    default: return launch_tc<kNT, 8, 2, 4>(NEGF_TC_ARGS);
+    case 5: return launch_tc<kNT, 8, 2, 4>(NEGF_TC_ARGS);
+    case 7: return launch_tc<kNT, 3, 1, 1, false, 2>(NEGF_TC_ARGS);
+    case 8: return launch_tc<kNT, 4, 2, 1, false, 2>(NEGF_TC_ARGS);
+    case 9: return launch_tc<kNT, 2, 1, 1, false, 3>(NEGF_TC_ARGS);
+    case 10: return launch_tc<kNT, 2, 2, 1, false, 4>(NEGF_TC_ARGS);
+    default: return launch_tc<kNT, 6, 1, 1>(NEGF_TC_ARGS);
   }
 #undef NEGF_TC_ARGS
 }
