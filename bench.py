@@ -32,11 +32,11 @@ WORK = dict(N=70, b=400, n_E=512, n_k=8, ge_frac=0.1, eta=1e-6, seed=1001,
 METRIC = "RGF energy-points/s (leads + forward/backward sweeps + observables + FP64 quadrature)"
 PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0)
 # DRAM bytes (read + write) of k_tc_gemm per 400 x 400 x 400 complex item, from the ncu capture
-# summarised in profiles/tc_gemm_b400_x64.md (64 items: 933.5 MB read + 153.8 MB written) of
+# summarised in profiles/tc_gemm_b400_x64.md (64 items: 930.8 MB read + 155.7 MB written) of
 # tensor-core configuration TC_PROFILED_CONFIG; reported only when the bench runs that
 # configuration.  The traffic of a launch scales with its items.
-TC_DRAM_BYTES_PER_ITEM_B400 = (933.452032e6 + 153.795072e6) / 64
-TC_PROFILED_CONFIG = 0
+TC_DRAM_BYTES_PER_ITEM_B400 = (930.753024e6 + 155.679488e6) / 64
+TC_PROFILED_CONFIG = 20
 
 
 def parse():
