@@ -397,6 +397,94 @@ __global__ void __launch_bounds__(256) k_slice(int n_lines, int K, int L, BMc<do
   }
 }
 
+// Slicing of 8 lines per CTA with the whole strip (8 lines x K complex values) held in shared
+// memory: the operand is read from memory once (the exponent pass and the digit pass both read
+// the strip), and each lane converts one complex value, so every slice store of a warp is one
+// contiguous 128-byte row segment.  Used when the strip fits (K up to kStripMaxK).
+constexpr int kStripLines = 8;
+constexpr int kStripMaxK = 858;  // 8 x (K + 1) x 16 B <= 110 KB: two CTAs per SM
+template <bool kB, int BETA, int S>
+__global__ void __launch_bounds__(256) k_slice_strip(int n_lines, int K, int L, BMc<double> X,
+                                                     int op, bool line_is_col,
+                                                     __nv_bfloat16* out, int32_t* eo,
+                                                     const int32_t* active) {
+  const int p = blockIdx.y;
+  if (active && !active[p]) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  z64* strip = reinterpret_cast<z64*>(smem_raw);  // [kStripLines][K + 1] (padded rows)
+  __shared__ int sexp[kStripLines];
+  const int lds = K + 1;
+  const int l0 = blockIdx.x * kStripLines;
+  const z64* x = bat(X, p);
+  const long long ld = X.ld;
+  const bool conj = (op == OP_C);
+  const z64 zero = mkc(0.0, 0.0);
+  // load the strip along the operand's memory layout (coalesced either way)
+  if (!line_is_col) {
+    for (int li = 0; li < kStripLines; ++li) {
+      const int line = l0 + li;
+      for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        z64 v = line < n_lines ? x[(long long)line * ld + k] : zero;
+        if (conj) v.im = -v.im;
+        strip[li * lds + k] = v;
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < kStripLines * K; e += blockDim.x) {
+      const int li = e & (kStripLines - 1), k = e / kStripLines;
+      const int line = l0 + li;
+      z64 v = line < n_lines ? x[(long long)k * ld + line] : zero;
+      if (conj) v.im = -v.im;
+      strip[li * lds + k] = v;
+    }
+  }
+  __syncthreads();
+  {  // scale exponent of each line: warp w reduces line w
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w < kStripLines) {
+      unsigned long long m = 0;
+      for (int k = lane; k < K; k += 32) {
+        const z64 v = strip[w * lds + k];
+        m = max(m, max(absbits(v.re), absbits(v.im)));
+      }
+      m = warp_max(m);
+      if (lane == 0) {
+        const int e = scale_exp(__longlong_as_double((long long)m));
+        sexp[w] = e;
+        if (l0 + w < n_lines) eo[(long long)p * n_lines + l0 + w] = e;
+      }
+    }
+  }
+  __syncthreads();
+  const long long rows_out = kB ? 2LL * n_lines : (long long)n_lines;
+  for (int li = 0; li < kStripLines; ++li) {
+    const int line = l0 + li;
+    if (line >= n_lines) break;
+    const int e = sexp[li];
+    for (int k = threadIdx.x; k < L / 2; k += blockDim.x) {
+      const z64 v = k < K ? strip[li * lds + k] : zero;
+      bool nr, ni;
+      const unsigned long long rr = fixed_point<BETA, S>(v.re, e, nr);
+      const unsigned long long ri = fixed_point<BETA, S>(v.im, e, ni);
+      Unroll<S>::run([&](auto sc) {
+        constexpr int sl = decltype(sc)::value;
+        const float fr = digit<BETA, S, sl>(rr, nr);
+        const float fi = digit<BETA, S, sl>(ri, ni);
+        __nv_bfloat16* base = out + ((long long)p * S + sl) * rows_out * L;
+        if (!kB) {
+          reinterpret_cast<__nv_bfloat162*>(base + (long long)line * L)[k] =
+              __floats2bfloat162_rn(fr, fi);
+        } else {
+          reinterpret_cast<__nv_bfloat162*>(base + (2LL * line) * L)[k] =
+              __floats2bfloat162_rn(fr, -fi);
+          reinterpret_cast<__nv_bfloat162*>(base + (2LL * line + 1) * L)[k] =
+              __floats2bfloat162_rn(fi, fr);
+        }
+      });
+    }
+  }
+}
+
 // ------------------------------------------------------------------ MMA kernel
 // CG = 1: one CTA computes a 128-row tile with tcgen05.mma.cta_group::1 (M = 128).
 // CG = 2: a cluster of two x-adjacent CTAs (consecutive row tiles) computes a 256-row tile with
@@ -1097,11 +1185,28 @@ template <bool kB>
 cudaError_t launch_slice(cudaStream_t s, int beta, int S, dim3 grid, int n_lines, int K, int L,
                          BMc<double> X, int op, bool line_is_col, __nv_bfloat16* out, int32_t* eo,
                          const int32_t* active) {
-#define NEGF_SLICE_CASE(B_, S_)                                                        \
-  if (beta == B_ && S == S_) {                                                         \
-    k_slice<kB, B_, S_><<<grid, 256, 0, s>>>(n_lines, K, L, X, op, line_is_col, out, eo, \
-                                             active);                                  \
-    return cudaGetLastError();                                                         \
+  const bool strip = K <= kStripMaxK;
+  const size_t strip_smem = (size_t)kStripLines * (K + 1) * sizeof(z64);
+  const dim3 sgrid((n_lines + kStripLines - 1) / kStripLines, grid.y);
+#define NEGF_SLICE_CASE(B_, S_)                                                             \
+  if (beta == B_ && S == S_) {                                                              \
+    if (strip) {                                                                            \
+      static bool attr = false;                                                             \
+      if (!attr) {                                                                          \
+        cudaError_t ea = cudaFuncSetAttribute(k_slice_strip<kB, B_, S_>,                    \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                              kStripLines * (kStripMaxK + 1) * 16);         \
+        if (ea != cudaSuccess) return ea;                                                   \
+        attr = true;                                                                        \
+      }                                                                                     \
+      k_slice_strip<kB, B_, S_><<<sgrid, 256, strip_smem, s>>>(n_lines, K, L, X, op,        \
+                                                                line_is_col, out, eo,       \
+                                                                active);                    \
+    } else {                                                                                \
+      k_slice<kB, B_, S_><<<grid, 256, 0, s>>>(n_lines, K, L, X, op, line_is_col, out, eo,  \
+                                               active);                                     \
+    }                                                                                       \
+    return cudaGetLastError();                                                              \
   }
   NEGF_SLICE_CASE(8, 6)
   NEGF_SLICE_CASE(7, 7)

@@ -34,9 +34,11 @@ def _bound(A, B, opA, opB):
     return K * a.max(axis=-1)[..., :, None] * b.max(axis=-2)[..., None, :]
 
 
-# M = 300 has an odd number (3) of 128-row tiles, which the CTA-pair kernel pads to an even count
+# M = 300 has an odd number (3) of 128-row tiles, which the CTA-pair kernel pads to an even count;
+# K = 1000 is longer than the operand strip the single-read slicing kernel keeps in shared
+# memory, so it takes the two-pass slicing kernel
 CASES = [(40, 40, 40), (77, 130, 50), (128, 128, 128), (200, 160, 96), (300, 200, 150),
-         (400, 400, 400)]
+         (400, 400, 400), (64, 48, 1000)]
 
 
 @pytest.mark.parametrize("prec", [0, 1])
