@@ -8,6 +8,7 @@
 // rank-nb update  A[:, rest] += Panel * A[pivot rows, rest]  (pivot rows zeroed first), which is
 // a batched GEMM.  The column permutation is undone at the end.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "profile.cuh"
@@ -268,6 +269,63 @@ __global__ void __launch_bounds__(kThreads) k_gj_panel(int n, int k0, int w, int
   }
 }
 
+// Trailing update of a Gauss-Jordan panel step: C += U T for every item, with U the eliminated
+// panel (n x w, row stride nb), T the pivot rows (w x n) and w <= kMaxPanel (FP32 only: the
+// FP64 blocks would not fit the static shared memory).  A 64 x 64 block of
+// C per CTA: the whole U and T blocks are staged in shared memory at once (one barrier), and C is
+// read into the accumulators before the multiply-adds so that its latency overlaps the staging.
+constexpr int kMaxPanel = 32;
+template <typename R>
+__global__ void __launch_bounds__(256) k_gj_update(int n, int w, int nb, const cx<R>* U,
+                                                   const cx<R>* T, BM<R> C,
+                                                   const int32_t* active) {
+  const int p = blockIdx.z;
+  if (active && !active[p]) return;
+  __shared__ cx<R> Us[kMaxPanel][65];  // padded: the staging writes walk down a column
+  __shared__ cx<R> Ts[kMaxPanel][64];
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const cx<R>* u = U + (long long)p * n * nb;
+  const cx<R>* t = T + (long long)p * nb * n;
+  cx<R>* c = bat(C, p);
+  const cx<R> zero = mkc<R>(R(0), R(0));
+  cx<R> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = m0 + ty + 16 * i, col = n0 + tx + 16 * j;
+      acc[i][j] = (r < n && col < n) ? c[(long long)r * C.ld + col] : zero;
+    }
+  for (int e = threadIdx.x; e < 64 * w; e += 256) {
+    const int r = e / w, k = e - r * w;  // U rows are w-contiguous
+    Us[k][r] = (m0 + r < n) ? u[(long long)(m0 + r) * nb + k] : zero;
+  }
+  for (int e = threadIdx.x; e < w * 64; e += 256) {
+    const int k = e >> 6, col = e & 63;
+    Ts[k][col] = (n0 + col < n) ? t[(long long)k * n + n0 + col] : zero;
+  }
+  __syncthreads();
+  for (int k = 0; k < w; ++k) {
+    cx<R> av[4], bv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) av[i] = Us[k][ty + 16 * i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) bv[j] = Ts[k][tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cfma(acc[i][j], av[i], bv[j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = m0 + ty + 16 * i, col = n0 + tx + 16 * j;
+      if (r < n && col < n) c[(long long)r * C.ld + col] = acc[i][j];
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_gj_unpermute(int n, BM<R> Am, BM<R> X,
                                                            const int32_t* piv,
@@ -342,12 +400,20 @@ cudaError_t gj_inverse(cudaStream_t s, int P, int n, BM<R> M, BM<R> X, cx<R>* U,
     prof_end(s, PROF_GJ_PANEL);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    BMc<R> Ua{U, (long long)n * nb, nullptr, nb};
-    BMc<R> Ta{T, (long long)nb * n, nullptr, n};
-    BMc<R> none{nullptr, 0, nullptr, 0};
-    e = gemm_simt<R>(s, P, n, n, w, mkc<double>(1.0, 0.0), Ua, OP_N, Ta, OP_N,
-                     mkc<double>(1.0, 0.0), M, mkc<double>(0.0, 0.0), none, active);
-    if (e != cudaSuccess) return e;
+    if constexpr (std::is_same<R, float>::value) {
+      // FP32: panels are at most kMaxPanel wide (gj_panel_width); FP64 is FMA-bound either way
+      k_gj_update<R><<<dim3((n + 63) / 64, (n + 63) / 64, P), 256, 0, s>>>(n, w, nb, U, T, M,
+                                                                         active);
+      count_launch();
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
+      BMc<R> Ua{U, (long long)n * nb, nullptr, nb};
+      BMc<R> Ta{T, (long long)nb * n, nullptr, n};
+      BMc<R> none{nullptr, 0, nullptr, 0};
+      e = gemm_simt<R>(s, P, n, n, w, mkc<double>(1.0, 0.0), Ua, OP_N, Ta, OP_N,
+                       mkc<double>(1.0, 0.0), M, mkc<double>(0.0, 0.0), none, active);
+      if (e != cudaSuccess) return e;
+    }
   }
   k_gj_unpermute<R><<<P, kThreads, n * sizeof(int), s>>>(n, M, X, piv, active);
   count_launch();
