@@ -1,6 +1,6 @@
 // Batched block inversion g = M^-1 of the sweeps of Eq. (1): Gauss-Jordan elimination with
-// partial pivoting.  Pivot magnitudes are compared in FP64 (largest |m|^2, lowest row on ties)
-// and the pivot reciprocal is taken in FP64 whatever the storage type R.
+// partial pivoting (largest |m|^2, lowest row on ties), magnitudes and pivot reciprocal in the
+// storage precision (the FP32 form is refined by Newton-Schulz steps afterwards).
 //
 // n <= small limit: one CTA per matrix, the whole matrix in shared memory.
 // larger n: blocked Gauss-Jordan.  A panel of nb columns is eliminated in shared memory, the
@@ -20,34 +20,45 @@ namespace {
 constexpr int kThreads = 256;
 constexpr size_t kSmemBudget = 180 * 1024;
 
+// |a|^2 in the storage precision (the entries of the blocks inverted here are between about
+// 1e-19 and 1e19 in magnitude, where the FP32 square neither overflows nor underflows).
 template <typename R>
-__device__ __forceinline__ double mag2(cx<R> a) {
-  return (double)a.re * (double)a.re + (double)a.im * (double)a.im;
+__device__ __forceinline__ R mag2(cx<R> a) {
+  return a.re * a.re + a.im * a.im;
 }
 
-// 1 / a in FP64, flagging an exactly zero pivot (replaced by a tiny number so the sweep goes on).
+// 1 / a, flagging an exactly zero pivot (replaced by a tiny number so the sweep goes on).  FP64
+// for FP64 storage; for FP32, a is first scaled by the power of two 2^-e that brings its larger
+// component into [0.5, 1), so |a'|^2 lies in [0.25, 2) and 1/a = conj(a') 2^-e / |a'|^2 loses
+// nothing to overflow or underflow.
 template <typename R>
 __device__ __forceinline__ cx<R> pivot_recip(cx<R> a, int32_t* st) {
-  z64 ad = mkc<double>((double)a.re, (double)a.im);
-  if (ad.re == 0.0 && ad.im == 0.0) {
+  if (a.re == R(0) && a.im == R(0)) {
     if (st) atomicOr(st, NEGF_PT_SINGULAR);
-    ad.re = sizeof(R) == 8 ? 1e-300 : 1e-30;
+    a.re = sizeof(R) == 8 ? R(1e-300) : R(1e-30);
   }
-  z64 d = crecip(ad);
-  return mkc<R>((R)d.re, (R)d.im);
+  if constexpr (sizeof(R) == 8) {
+    return crecip(a);
+  } else {
+    int e;
+    frexpf(fmaxf(fabsf(a.re), fabsf(a.im)), &e);
+    const float ar = ldexpf(a.re, -e), ai = ldexpf(a.im, -e);
+    const float inv = ldexpf(1.0f / (ar * ar + ai * ai), -e);
+    return mkc<float>(ar * inv, -ai * inv);
+  }
 }
 
 // Per-CTA scratch of one Gauss-Jordan column step.
 template <typename R>
 struct GjScratch {
-  double sv[32];
+  R sv[32];
   int si[32];
   cx<R> d;
 };
 
 // One Gauss-Jordan step on column jj of the shared-memory array P (rows x w, row stride w):
-// pivot search over rows [j, rows) (largest |m|^2 compared in FP64, lowest row on ties), swap
-// of rows j and the pivot row, pivot reciprocal in FP64, and elimination of column jj from all
+// pivot search over rows [j, rows) (largest |m|^2, lowest row on ties), swap of rows j and the
+// pivot row, pivot reciprocal (pivot_recip), and elimination of column jj from all
 // other rows.  f[rows] and prow[w] are shared scratch.  Three block barriers per column:
 //   (1) after the per-warp argmax, (2) after the swap / column copy / reciprocal, (3) after the
 //   update.  Every thread combines the per-warp winners itself, and the elimination scales the
@@ -57,17 +68,17 @@ template <typename R>
 __device__ int gj_column(cx<R>* P, int rows, int w, int j, int jj, cx<R>* f, cx<R>* prow,
                          GjScratch<R>& sc, int32_t* st) {
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, wid = tid >> 5;
-  double best = -1.0;
+  R best = R(-1);
   int bi = rows;
   for (int r = j + tid; r < rows; r += bd) {
-    const double v = mag2(P[(long long)r * w + jj]);
+    const R v = mag2(P[(long long)r * w + jj]);
     if (v > best) {
       best = v;
       bi = r;
     }
   }
   for (int off = 16; off > 0; off >>= 1) {
-    const double ov = __shfl_down_sync(0xffffffffu, best, off);
+    const R ov = __shfl_down_sync(0xffffffffu, best, off);
     const int oi = __shfl_down_sync(0xffffffffu, bi, off);
     if (ov > best || (ov == best && oi < bi)) {
       best = ov;
@@ -79,7 +90,7 @@ __device__ int gj_column(cx<R>* P, int rows, int w, int j, int jj, cx<R>* f, cx<
     sc.si[wid] = bi;
   }
   __syncthreads();  // (1)
-  double b = sc.sv[0];
+  R b = sc.sv[0];
   int pi = sc.si[0];
   const int nw = bd >> 5;
   for (int k = 1; k < nw; ++k)
@@ -105,26 +116,40 @@ __device__ int gj_column(cx<R>* P, int rows, int w, int j, int jj, cx<R>* f, cx<
   __syncthreads();  // (2)
   const cx<R> d = sc.d;
   if (w <= bd) {
+    // Thread (r0, c) updates rows r0, r0 + rstep, ...  of column c, four rows per batch with the
+    // loads ahead of the stores (P and f are disjoint).  The pivot column (c == jj) starts from 0
+    // so that it becomes -f[r] d; row j is computed like the others and then overwritten with the
+    // scaled pivot row by the thread that owns it.
     const int c = tid % w;
     const int r0 = tid / w, rstep = bd / w;
     if (r0 < rstep) {
-      const cx<R> pj = (c == jj) ? d : prow[c] * d;
-      for (int r = r0; r < rows; r += rstep) {
-        cx<R>* e = P + (long long)r * w + c;
-        if (r == j) {
-          *e = pj;
-        } else {
-          const cx<R> fr = f[r];
-          if (c == jj) {
-            *e = mkc<R>(R(0), R(0)) - fr * d;
-          } else {
-            cx<R> v = *e;
-            v.re = v.re - (fr.re * pj.re - fr.im * pj.im);
-            v.im = v.im - (fr.re * pj.im + fr.im * pj.re);
-            *e = v;
-          }
+      const bool pcol = (c == jj);
+      const cx<R> pj = pcol ? d : prow[c] * d;
+      const cx<R> zero = mkc<R>(R(0), R(0));
+      int r = r0;
+      for (; r + 3 * rstep < rows; r += 4 * rstep) {
+        cx<R> v[4], fr[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[u] = P[(long long)(r + u * rstep) * w + c];
+          fr[u] = f[r + u * rstep];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          cx<R> x = pcol ? zero : v[u];
+          x.re = x.re - (fr[u].re * pj.re - fr[u].im * pj.im);
+          x.im = x.im - (fr[u].re * pj.im + fr[u].im * pj.re);
+          P[(long long)(r + u * rstep) * w + c] = x;
         }
       }
+      for (; r < rows; r += rstep) {
+        const cx<R> fr = f[r];
+        cx<R> x = pcol ? zero : P[(long long)r * w + c];
+        x.re = x.re - (fr.re * pj.re - fr.im * pj.im);
+        x.im = x.im - (fr.re * pj.im + fr.im * pj.re);
+        P[(long long)r * w + c] = x;
+      }
+      if (j % rstep == r0) P[(long long)j * w + c] = pj;
     }
   } else {
     for (int r = 0; r < rows; ++r) {
@@ -208,9 +233,19 @@ __global__ void __launch_bounds__(kThreads) k_gj_panel(int n, int k0, int w, int
   cx<R>* a = bat(Am, p);
   const long long ld = Am.ld;
   int32_t* pv = piv + (long long)p * n;
-  for (int r = threadIdx.x / w; r < n; r += blockDim.x / w) {
-    const int c = threadIdx.x % w;
-    if (threadIdx.x / w < (int)blockDim.x / w) P[(long long)r * w + c] = a[r * ld + k0 + c];
+  {
+    // the panel columns, eight rows per batch with the loads ahead of the stores
+    const int c = threadIdx.x % w, r0 = threadIdx.x / w, rs = blockDim.x / w;
+    if (r0 < rs)
+      for (int rb = r0; rb < n; rb += 8 * rs) {
+        cx<R> v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (rb + u * rs < n) v[u] = a[(long long)(rb + u * rs) * ld + k0 + c];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (rb + u * rs < n) P[(long long)(rb + u * rs) * w + c] = v[u];
+      }
   }
   for (int r = threadIdx.x; r < n; r += blockDim.x) cont[r] = r;
   __syncthreads();
@@ -297,13 +332,27 @@ __global__ void __launch_bounds__(256) k_gj_update(int n, int w, int nb, const c
       const int r = m0 + ty + 16 * i, col = n0 + tx + 16 * j;
       acc[i][j] = (r < n && col < n) ? c[(long long)r * C.ld + col] : zero;
     }
-  for (int e = threadIdx.x; e < 64 * w; e += 256) {
-    const int r = e / w, k = e - r * w;  // U rows are w-contiguous
-    Us[k][r] = (m0 + r < n) ? u[(long long)(m0 + r) * nb + k] : zero;
+  // staging: slot e of U is (row e / 32, column e % 32), of T (row e / 64, column e % 64); all
+  // loads are issued before the first shared-memory store
+  constexpr int kPer = kMaxPanel * 64 / 256;
+  cx<R> us[kPer], ts[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int e = threadIdx.x + 256 * q;
+    const int r = e >> 5, k = e & 31;
+    us[q] = (k < w && m0 + r < n) ? u[(long long)(m0 + r) * nb + k] : zero;
   }
-  for (int e = threadIdx.x; e < w * 64; e += 256) {
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int e = threadIdx.x + 256 * q;
     const int k = e >> 6, col = e & 63;
-    Ts[k][col] = (n0 + col < n) ? t[(long long)k * n + n0 + col] : zero;
+    ts[q] = (k < w && n0 + col < n) ? t[(long long)k * n + n0 + col] : zero;
+  }
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int e = threadIdx.x + 256 * q;
+    Us[e & 31][e >> 5] = us[q];
+    Ts[e >> 6][e & 63] = ts[q];
   }
   __syncthreads();
   for (int k = 0; k < w; ++k) {
