@@ -94,6 +94,31 @@ def point_index(n_pts_total, start, count):
     return idx // WORK["n_E"], idx % WORK["n_E"]   # (k index, energy index)
 
 
+def rank_points(step, rank, world, P):
+    """(k index, energy index) of the P points that rank `rank` of `world` solves in `step`:
+    consecutive blocks of P points of the (k, E) grid dealt out to the ranks in turn, so ranks
+    solve disjoint points and `world` ranks solve `world` times the points of one (weak scaling,
+    no data-path collective)."""
+    n_tot = WORK["n_E"] * WORK["n_k"]
+    return point_index(n_tot, (step * world + rank) * P, P)
+
+
+def max_over_ranks(ms, dist, device):
+    """Length of the timed region as the slowest rank measured it (every rank gets it)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def aggregate_rate(steps, P, world, ms):
+    """Whole-job points per second: the points all ranks solved over the slowest rank's time."""
+    return steps * P * world / (ms / 1e3)
+
+
 class Clocks:
     """nvidia-smi sampling (read-only) while the timed region runs."""
 
@@ -342,12 +367,11 @@ def main():
             from paper_1510_04686_gb300 import autotune
             tuned = autotune.tune_tc(WORK["b"], P)["config"]
     opt = negf.options(precision=prec, chunk=P)
-    n_tot = WORK["n_E"] * WORK["n_k"]
     total_steps = args.warmup + args.steps
-    # per-step index tensors (rank-strided so ranks solve disjoint points)
+    # per-step index tensors (ranks solve disjoint points)
     step_E, step_sys, step_w = [], [], []
     for s in range(total_steps):
-        kk, ee = point_index(n_tot, (s * world + rank) * P, P)
+        kk, ee = rank_points(s, rank, world, P)
         step_E.append(torch.as_tensor(E[ee], device=dvc))
         step_sys.append(torch.as_tensor(kk.astype(np.int32), device=dvc))
         step_w.append(torch.as_tensor(wE[ee] * wk[kk], device=dvc))
@@ -389,18 +413,12 @@ def main():
         torch.cuda.nvtx.range_pop()
     launches = negf.launch_count() - l0
     negf.profile(False)
-    ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([ms], device=dvc)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dvc)
     n_launch, tc_ms, alg, hw = negf.profile_read(negf.PROF_TC_GEMM)
     sl_n, sl_ms, _, _ = negf.profile_read(negf.PROF_SLICE)
     inv_n, inv_ms, _, _ = negf.profile_read(negf.PROF_INV)
     pan_n, pan_ms, _, _ = negf.profile_read(negf.PROF_GJ_PANEL)
-    points = args.steps * P * world
-    value = points / (ms / 1e3)
+    value = aggregate_rate(args.steps, P, world, ms)
 
     pk, pk_kind = peaks()
     peak_bf16 = pk.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"])
@@ -433,7 +451,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORK["name"], "points_per_step": P, "precision": args.precision,
                    "l2": "inputs > L2: each step streams 358 MB of H blocks",
-                   "parallelism": f"replicas x{world}", "tc_config": tuned},
+                   "parallelism": f"points sharded over {world} rank(s), no data-path collective", "tc_config": tuned},
         "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roofline,
     }
     if rank == 0 and not args.no_extras:

@@ -1,0 +1,85 @@
+"""Stored oracle values of the small ballistic workload (tests/golden/config0_oracle.json).
+
+The paper prints no worked example, so the fixture is written by tests/golden/make_golden.py from
+the oracle alone (its own pins are in test_oracle_pins.py).  The CPU test checks that the oracle
+still reproduces the fixture; the GPU tests check the CUDA path against it without running the
+oracle on the GPU host.  Bars: FP64 form 1e-9 of each quantity's scale per point (the
+per-point bar of the other FP64 parity tests), mixed form 1e-6 per point and on the integrals.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import config_workload
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config0_oracle.json")
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        g = json.load(f)
+    for k in ("E", "transmission", "slab_density", "current", "integrated_slab_density",
+              "integrated_current"):
+        g[k] = np.asarray(g[k])
+    return g
+
+
+def _err(a, b):
+    return np.abs(np.asarray(a) - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def test_oracle_reproduces_golden(golden):
+    w = config_workload(0)
+    dev, E, wE, eta = w["device"], w["E"], w["wE"], w["eta"]
+    N, b = golden["N"], golden["b"]
+    assert np.allclose(E[golden["energy_index"]], golden["E"], rtol=0, atol=1e-15)
+    pts = [O.solve_point(dev.D, dev.T, float(e), eta, None, eta_lead=eta) for e in E]
+    slab = np.array([p["density"].reshape(N, b).sum(axis=1) for p in pts])
+    cur = np.array([p["current"] for p in pts])
+    T = np.array([p["transmission"] for p in pts])
+    sel = golden["energy_index"]
+    assert _err(T[sel], golden["transmission"]) < 1e-9
+    assert _err(slab[sel], golden["slab_density"]) < 1e-9
+    assert _err(cur[sel], golden["current"]) < 1e-9
+    assert _err(O.integrate(list(slab), wE), golden["integrated_slab_density"]) < 1e-9
+    assert _err(O.integrate(list(cur), wE), golden["integrated_current"]) < 1e-9
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_cuda_path_matches_golden(golden, prec):
+    torch = pytest.importorskip("torch")
+    negf = pytest.importorskip("paper_1510_04686_gb300")
+    negf._build.build()
+    negf.library()
+    w = config_workload(0)
+    dev = w["device"]
+    N, b = golden["N"], golden["b"]
+    d = negf.Device(torch.as_tensor(dev.D[None], device="cuda"),
+                    torch.as_tensor(dev.T[None], device="cuda"))
+    E = torch.as_tensor(w["E"], device="cuda")
+    st = torch.zeros(len(w["E"]), dtype=torch.int32, device="cuda")
+    opt = negf.options(precision=negf.PREC_FP64 if prec == "fp64" else negf.PREC_MIXED)
+    lead = negf.lead_selfenergy(d, E, st, opt)
+    out = negf.rgf_solve(d, E, st, lead["sigma_R"], lead["sigma_L"], opt)
+    wE = torch.as_tensor(w["wE"], device="cuda")
+    slab_t = out["density"].reshape(len(w["E"]), N, b).sum(dim=2)
+    n_int = negf.integrate(slab_t, wE).cpu().numpy()
+    j_int = negf.integrate(out["current"], wE).cpu().numpy()
+    torch.cuda.synchronize()
+    assert np.all(out["status"].cpu().numpy() == 0)
+    sel = golden["energy_index"]
+    slab = slab_t.cpu().numpy()[sel]
+    cur = out["current"].cpu().numpy()[sel]
+    T = out["transmission"].cpu().numpy()[sel]
+    bar = 1e-9 if prec == "fp64" else 1e-6
+    e_n, e_j = _err(slab, golden["slab_density"]), _err(cur, golden["current"])
+    e_T = np.abs(T - golden["transmission"]).max() / max(1.0, np.abs(golden["transmission"]).max())
+    print(f"{prec}: slab density {e_n:.2e} current {e_j:.2e} T {e_T:.2e}")
+    assert e_n < bar and e_j < bar and e_T < bar
+    assert _err(n_int, golden["integrated_slab_density"]) < max(bar, 1e-9)
+    assert _err(j_int, golden["integrated_current"]) < max(bar, 1e-9)
