@@ -234,8 +234,9 @@ negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, in
                                void* ws, size_t ws_bytes, void* stream);
 
 /* Batched block inverse X[p] = M[p]^-1 (the (z - H - Sigma)^-1 of Eq. 1), n x n complex128,
- * contiguous items.  Gauss-Jordan with partial pivoting (largest |m|^2, lowest row on ties),
- * pivot search and reciprocal in the storage precision.
+ * contiguous items.  Gauss-Jordan with partial pivoting (largest |m|^2, lowest row on ties;
+ * magnitudes in FP64, or as exact FP32 pairs to about 2^-47 in the mixed form's FP32
+ * elimination), pivot reciprocal in the storage precision.
  * FP64 form: FP64 elimination, M is destroyed.  Mixed form: FP32 elimination followed by
  * `refine_steps` Newton-Schulz steps X <- X + X (I - M X) with tensor-core products; M is
  * kept.  status[p] gets NEGF_PT_SINGULAR on an exactly zero pivot. */

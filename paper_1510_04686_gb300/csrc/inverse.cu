@@ -1,6 +1,7 @@
 // Batched block inversion g = M^-1 of the sweeps of Eq. (1): Gauss-Jordan elimination with
-// partial pivoting (largest |m|^2, lowest row on ties), magnitudes and pivot reciprocal in the
-// storage precision (the FP32 form is refined by Newton-Schulz steps afterwards).
+// partial pivoting (largest |m|^2, lowest row on ties; magnitudes to FP64 accuracy, as FP32 pairs
+// for FP32 storage) and the pivot reciprocal in the storage precision (the FP32 form is refined
+// by Newton-Schulz steps afterwards).
 //
 // n <= small limit: one CTA per matrix, the whole matrix in shared memory.
 // larger n: blocked Gauss-Jordan.  A panel of nb columns is eliminated in shared memory, the
@@ -20,11 +21,35 @@ namespace {
 constexpr int kThreads = 256;
 constexpr size_t kSmemBudget = 180 * 1024;
 
-// |a|^2 in the storage precision (the entries of the blocks inverted here are between about
-// 1e-19 and 1e19 in magnitude, where the FP32 square neither overflows nor underflows).
+// Pivot magnitude |a|^2 = hi + lo.  FP64 storage: hi = |a|^2 in FP64, lo = 0.  FP32 storage: the
+// exact squares as FP32 pairs (product and its fmaf residual) and the exact sum of the leading
+// parts (TwoSum), so hi + lo carries about 48 bits: an FP64-class pivot decision without the
+// FP64 pipe.  Intrinsics keep the compiler from fusing the steps.  (The entries of the blocks
+// inverted here lie between about 1e-19 and 1e19 in magnitude, where no square over- or
+// underflows in FP32.)
 template <typename R>
-__device__ __forceinline__ R mag2(cx<R> a) {
-  return a.re * a.re + a.im * a.im;
+struct Mag {
+  R hi, lo;
+};
+template <typename R>
+__device__ __forceinline__ Mag<R> mag2(cx<R> a) {
+  if constexpr (sizeof(R) == 8) {
+    return Mag<R>{a.re * a.re + a.im * a.im, 0.0};
+  } else {
+    const float p = __fmul_rn(a.re, a.re), q = __fmul_rn(a.im, a.im);
+    const float ep = fmaf(a.re, a.re, -p), eq = fmaf(a.im, a.im, -q);
+    const float s = __fadd_rn(p, q);
+    const float bq = __fsub_rn(s, p);
+    const float t = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bq)), __fsub_rn(q, bq));
+    return Mag<R>{s, __fadd_rn(t, __fadd_rn(ep, eq))};
+  }
+}
+// a (row ia) is a better pivot than b (row ib): larger magnitude, lower row on ties.  The sign of
+// (a.hi - b.hi) + (a.lo - b.lo) is that of the exact difference except within FP64-level ties.
+template <typename R>
+__device__ __forceinline__ bool better(Mag<R> a, int ia, Mag<R> b, int ib) {
+  const R d = (a.hi - b.hi) + (a.lo - b.lo);
+  return d > R(0) || (d == R(0) && ia < ib);
 }
 
 // 1 / a, flagging an exactly zero pivot (replaced by a tiny number so the sweep goes on).  FP64
@@ -51,7 +76,7 @@ __device__ __forceinline__ cx<R> pivot_recip(cx<R> a, int32_t* st) {
 // Per-CTA scratch of one Gauss-Jordan column step.
 template <typename R>
 struct GjScratch {
-  R sv[32];
+  Mag<R> sv[32];
   int si[32];
   cx<R> d;
 };
@@ -68,19 +93,20 @@ template <typename R>
 __device__ int gj_column(cx<R>* P, int rows, int w, int j, int jj, cx<R>* f, cx<R>* prow,
                          GjScratch<R>& sc, int32_t* st) {
   const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31, wid = tid >> 5;
-  R best = R(-1);
+  Mag<R> best{R(-1), R(0)};
   int bi = rows;
   for (int r = j + tid; r < rows; r += bd) {
-    const R v = mag2(P[(long long)r * w + jj]);
-    if (v > best) {
+    const Mag<R> v = mag2(P[(long long)r * w + jj]);
+    if (better(v, r, best, bi)) {
       best = v;
       bi = r;
     }
   }
   for (int off = 16; off > 0; off >>= 1) {
-    const R ov = __shfl_down_sync(0xffffffffu, best, off);
+    const Mag<R> ov{__shfl_down_sync(0xffffffffu, best.hi, off),
+                    __shfl_down_sync(0xffffffffu, best.lo, off)};
     const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-    if (ov > best || (ov == best && oi < bi)) {
+    if (better(ov, oi, best, bi)) {
       best = ov;
       bi = oi;
     }
@@ -90,11 +116,11 @@ __device__ int gj_column(cx<R>* P, int rows, int w, int j, int jj, cx<R>* f, cx<
     sc.si[wid] = bi;
   }
   __syncthreads();  // (1)
-  R b = sc.sv[0];
+  Mag<R> b = sc.sv[0];
   int pi = sc.si[0];
   const int nw = bd >> 5;
   for (int k = 1; k < nw; ++k)
-    if (sc.sv[k] > b || (sc.sv[k] == b && sc.si[k] < pi)) {
+    if (better(sc.sv[k], sc.si[k], b, pi)) {
       b = sc.sv[k];
       pi = sc.si[k];
     }

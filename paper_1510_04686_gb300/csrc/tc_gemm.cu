@@ -419,23 +419,34 @@ __global__ void __launch_bounds__(256) k_slice_strip(int n_lines, int K, int L, 
   const long long ld = X.ld;
   const bool conj = (op == OP_C);
   const z64 zero = mkc(0.0, 0.0);
-  // load the strip along the operand's memory layout (coalesced either way)
-  if (!line_is_col) {
-    for (int li = 0; li < kStripLines; ++li) {
-      const int line = l0 + li;
-      for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        z64 v = line < n_lines ? x[(long long)line * ld + k] : zero;
-        if (conj) v.im = -v.im;
-        strip[li * lds + k] = v;
+  // load the strip along the operand's memory layout (coalesced either way): element e is
+  // (line e / K, k = e % K) for row lines and (line e % 8, k = e / 8) for column lines; eight
+  // loads per thread are in flight before their shared-memory stores
+  const int tot = kStripLines * K;
+  for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * 256) {
+    z64 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256;
+      v[u] = zero;
+      if (e < tot) {
+        const int li = line_is_col ? (e & (kStripLines - 1)) : e / K;
+        const int k = line_is_col ? e / kStripLines : e - li * K;
+        const int line = l0 + li;
+        if (line < n_lines)
+          v[u] = line_is_col ? x[(long long)k * ld + line] : x[(long long)line * ld + k];
       }
     }
-  } else {
-    for (int e = threadIdx.x; e < kStripLines * K; e += blockDim.x) {
-      const int li = e & (kStripLines - 1), k = e / kStripLines;
-      const int line = l0 + li;
-      z64 v = line < n_lines ? x[(long long)k * ld + line] : zero;
-      if (conj) v.im = -v.im;
-      strip[li * lds + k] = v;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * 256;
+      if (e < tot) {
+        const int li = line_is_col ? (e & (kStripLines - 1)) : e / K;
+        const int k = line_is_col ? e / kStripLines : e - li * K;
+        z64 w = v[u];
+        if (conj) w.im = -w.im;
+        strip[li * lds + k] = w;
+      }
     }
   }
   __syncthreads();
