@@ -1092,6 +1092,19 @@ Sched build_sched(int S, int n_chunks, int n_parts) {
   return sc;
 }
 
+// Kernel attributes (the dynamic shared-memory limit) belong to a device context, so each
+// kernel records, per device (ordinals below 32), whether it has set them there.
+static cudaError_t set_smem_once(std::atomic<unsigned>& done, const void* fn, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned bit = 1u << (dev & 31);
+  if (done.load() & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit);
+  return e;
+}
+
 template <int NT, int STAGES, int CG, int G, bool WIN = false, int KPS = 1>
 cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S, int two_beta,
                       int n_parts, const CUtensorMap& mA, const CUtensorMap& mB, const TcWs& ws,
@@ -1099,12 +1112,11 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
                       z64 beta, z64 gamma, BM<double> C, BMc<double> D, bool add_identity,
                       int trunc_beta, const int32_t* active) {
   using CF = Cfg<NT, STAGES, CG, G, KPS>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<NT, STAGES, CG, G, WIN, KPS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, CF::kSmem);
+  static std::atomic<unsigned> attr{0};
+  {
+    cudaError_t e = set_smem_once(
+        attr, reinterpret_cast<const void*>(&k_tc_gemm<NT, STAGES, CG, G, WIN, KPS>), CF::kSmem);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   if ((long long)std::min(n_parts, kMaxParts) * S * (S + 1) / 2 > kMaxItems)
     return cudaErrorInvalidValue;  // schedule longer than the kernel's item table
@@ -1202,14 +1214,11 @@ cudaError_t launch_slice(cudaStream_t s, int beta, int S, dim3 grid, int n_lines
 #define NEGF_SLICE_CASE(B_, S_)                                                             \
   if (beta == B_ && S == S_) {                                                              \
     if (strip) {                                                                            \
-      static bool attr = false;                                                             \
-      if (!attr) {                                                                          \
-        cudaError_t ea = cudaFuncSetAttribute(k_slice_strip<kB, B_, S_>,                    \
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                              kStripLines * (kStripMaxK + 1) * 16);         \
-        if (ea != cudaSuccess) return ea;                                                   \
-        attr = true;                                                                        \
-      }                                                                                     \
+      static std::atomic<unsigned> attr{0};                                                 \
+      cudaError_t ea = set_smem_once(                                                       \
+          attr, reinterpret_cast<const void*>(&k_slice_strip<kB, B_, S_>),                  \
+          kStripLines * (kStripMaxK + 1) * 16);                                             \
+      if (ea != cudaSuccess) return ea;                                                     \
       k_slice_strip<kB, B_, S_><<<sgrid, 256, strip_smem, s>>>(n_lines, K, L, X, op,        \
                                                                 line_is_col, out, eo,       \
                                                                 active);                    \
