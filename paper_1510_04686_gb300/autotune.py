@@ -21,12 +21,28 @@ def _key(b, batch):
     return os.path.join(CACHE, f"tc_{name}_b{b}_n{batch}.json")
 
 
+def load_cached(path: str):
+    """The cached record at `path`, or None when there is none or it was written for another set
+    of configurations (a library with a different configuration count)."""
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if not isinstance(rec, dict):
+        return None
+    n = _n.tc_config_count()
+    c = rec.get("config")
+    if rec.get("n_configs") != n or not isinstance(c, int) or not 0 <= c < n:
+        return None
+    return rec
+
+
 def tune_tc(b: int, batch: int, reps: int = 3, use_cache: bool = True) -> dict:
     """Select and return the best configuration for b x b x b products in batches of `batch`."""
     path = _key(b, batch)
-    if use_cache and os.path.exists(path):
-        with open(path) as fh:
-            rec = json.load(fh)
+    rec = load_cached(path) if use_cache else None
+    if rec is not None:
         _n.tc_config(rec["config"])
         return rec
     g = torch.Generator(device="cuda").manual_seed(1)
@@ -47,7 +63,7 @@ def tune_tc(b: int, batch: int, reps: int = 3, use_cache: bool = True) -> dict:
         times[c] = e0.elapsed_time(e1) / reps
     best = min(times, key=times.get)
     _n.tc_config(best)
-    rec = {"b": b, "batch": batch, "config": best, "ms": times}
+    rec = {"b": b, "batch": batch, "config": best, "n_configs": _n.tc_config_count(), "ms": times}
     os.makedirs(CACHE, exist_ok=True)
     with open(path, "w") as fh:
         json.dump(rec, fh)

@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI: the library loads, exports every declared symbol, and rejects
 bad arguments before any CUDA call (so these run without a GPU)."""
 import ctypes
+import json
 import os
 import re
 
@@ -112,3 +113,25 @@ def test_options_struct_layout():
     assert ctypes.sizeof(B._Dev) == 4 * 4 + 2 * 8
     o = negf.options()
     assert o.sr_host_check == 4
+
+
+def test_autotune_cache_rejects_stale_records(tmp_path):
+    """A cached tensor-core choice is reused only if it was written for this library's set of
+    configurations."""
+    from paper_1510_04686_gb300 import autotune
+    n = autotune._n.tc_config_count()
+    good = tmp_path / "good.json"
+    good.write_text(json.dumps({"b": 400, "batch": 8, "config": n - 1, "n_configs": n}))
+    assert autotune.load_cached(str(good))["config"] == n - 1
+    for bad in ({"b": 400, "batch": 8, "config": 1},                        # no count
+                {"b": 400, "batch": 8, "config": 1, "n_configs": n + 3},    # other library
+                {"b": 400, "batch": 8, "config": n, "n_configs": n},        # out of range
+                {"b": 400, "batch": 8, "config": "1", "n_configs": n}):
+        p = tmp_path / "bad.json"
+        p.write_text(json.dumps(bad))
+        assert autotune.load_cached(str(p)) is None
+    (tmp_path / "list.json").write_text("[1, 2]")
+    assert autotune.load_cached(str(tmp_path / "list.json")) is None
+    (tmp_path / "junk.json").write_text("{not json")
+    assert autotune.load_cached(str(tmp_path / "junk.json")) is None
+    assert autotune.load_cached(str(tmp_path / "missing.json")) is None
