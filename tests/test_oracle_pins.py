@@ -295,3 +295,43 @@ def test_acoustic_scba_conserves_current_per_energy():
     # scattering changes the current relative to the ballistic Landauer value
     o_b = O.solve_point(dev.D, dev.T, E[2], 0.0, None, eta_lead=1e-7)
     assert abs(outs[2]["current"][0] - o_b["current"][0]) > 1e-6 * abs(o_b["current"][0])
+
+
+def _born_fdt_violation(dev, E_max, shift, n_iter=2, dE=0.02, D_ac=0.002, D_op=0.004):
+    """Max over energies of |G^<_jj - i f A_jj| / max_j |A_jj| after n_iter Born updates at
+    equilibrium (mu_L = mu_R = 0, no device eta)."""
+    E = np.arange(-E_max, E_max + dE / 2, dE)
+    N, b = dev.N, dev.b
+    n0 = O.bose(abs(shift) * dE, KT)
+    sR = np.zeros((len(E), N * b), dtype=complex)
+    sL = np.zeros_like(sR)
+    for _ in range(n_iter + 1):
+        outs = [O.solve_point(dev.D, dev.T, e, 0.0, None, eta_lead=1e-7, mu_L=0.0, mu_R=0.0,
+                              kT=KT, sR=sR[i].reshape(N, b), sL=sL[i].reshape(N, b))
+                for i, e in enumerate(E)]
+        dGR = np.array([o["diagGR"] for o in outs])[None]
+        dGL = np.array([o["diagGL"] for o in outs])[None]
+        sR, sL, _ = O.scba_step(dGR, dGL, np.ones(1), D_ac, D_op, shift, n0, sR, sL)
+    f = 1.0 / (np.exp(E / KT) + 1.0)
+    worst = 0.0
+    for i, o in enumerate(outs):
+        A = 1j * (o["diagGR"] - o["diagGR"].conj())
+        worst = max(worst, np.abs(o["diagGL"] - 1j * f[i] * A).max() / np.abs(A).max())
+    return worst
+
+
+def test_scba_keeps_equilibrium_detailed_balance():
+    """At equilibrium every Born update of Eqs. (4)-(6) keeps G^< = -f (G^R - G^A) = i f A.
+
+    If G^< = i f A at all energies, the optical terms pair (1 + n0) G^<(E + hw) in Sigma^< with
+    n0 G^>(E + hw) in Sigma^> (and n0 G^<(E - hw) with (1 + n0) G^>(E - hw)).  Fermi and Bose
+    factors at one temperature satisfy (1 + n0) f(E + hw) (1 - f(E)) = n0 (1 - f(E + hw)) f(E),
+    so every pair obeys the KMS relation Sigma^< (1 - f) = -f Sigma^> on its own (grid
+    truncation drops whole pairs), and the next G^< = G^R Sigma^< G^A is i f A again: the check
+    is exact at every energy.  Exchanging emission and absorption (the sign of the energy shift,
+    a mistake planted here in the oracle's input) breaks it.
+    """
+    for dev, E_max in ((chain_device(6, 0.0, 0.1), 0.6),
+                       (channel_device(4, 3, 21, d_lo=-0.1, d_hi=0.1), 0.8)):
+        assert _born_fdt_violation(dev, E_max, 3) < 1e-12
+        assert _born_fdt_violation(dev, E_max, -3) > 1e-4
