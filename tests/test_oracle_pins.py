@@ -335,3 +335,49 @@ def test_scba_keeps_equilibrium_detailed_balance():
                        (channel_device(4, 3, 21, d_lo=-0.1, d_hi=0.1), 0.8)):
         assert _born_fdt_violation(dev, E_max, 3) < 1e-12
         assert _born_fdt_violation(dev, E_max, -3) > 1e-4
+
+
+def _optical_born_currents(dev, n0_lesser_factor=1.0, shift=3, dE=0.02, E_max=0.8, D_op=0.004):
+    """Born loop with optical phonons only (Eqs. 5-6) at the default bias, to |dSigma| < 1e-12;
+    returns the bond currents j_i(E).  n0_lesser_factor != 1 plants a mistake in the oracle's
+    update: Sigma^< then uses another phonon occupation than Sigma^R."""
+    E = np.arange(-E_max, E_max + dE / 2, dE)
+    N, b = dev.N, dev.b
+    n0 = O.bose(shift * dE, KT)
+    sR = np.zeros((len(E), N * b), dtype=complex)
+    sL = np.zeros_like(sR)
+
+    def solve():
+        return [O.solve_point(dev.D, dev.T, e, 0.0, None, eta_lead=1e-7, sR=sR[i].reshape(N, b),
+                              sL=sL[i].reshape(N, b)) for i, e in enumerate(E)]
+
+    for _ in range(60):
+        outs = solve()
+        dGR = np.array([o["diagGR"] for o in outs])[None]
+        dGL = np.array([o["diagGL"] for o in outs])[None]
+        nR, nL = O.scba_selfenergy(dGR, dGL, np.ones(1), 0.0, D_op, shift, n0)
+        if n0_lesser_factor != 1.0:
+            _, nL = O.scba_selfenergy(dGR, dGL, np.ones(1), 0.0, D_op, shift, n0_lesser_factor * n0)
+        delta = max(np.abs(nR - sR).max(), np.abs(nL - sL).max())
+        sR, sL = nR, nL
+        if delta < 1e-12:
+            break
+    assert delta < 1e-12
+    return np.array([o["current"] for o in solve()]), dE
+
+
+def test_optical_scba_conserves_energy_integrated_current():
+    """Inelastic scattering moves electrons between energies, so j_i(E) differs from bond to bond,
+    but at convergence of Eqs. (5)-(6) no particle is lost: the energy integral of j_i is the
+    same on every bond.  Each in-scattering term of Sigma^<(E) from E +- hw meets the matching
+    out-scattering term of Sigma^>(E +- hw) (energies shifted off the grid drop both), so the
+    balance is exact.  A Sigma^< whose phonon occupation differs from that of Sigma^R (planted)
+    breaks it."""
+    dev = channel_device(4, 3, 21, d_lo=-0.1, d_hi=0.1)
+    J, dE = _optical_born_currents(dev)
+    J_int = J.sum(axis=0) * dE
+    assert np.abs(J_int - J_int.mean()).max() < 1e-10 * np.abs(J_int).max()
+    assert np.abs(J - J.mean(axis=1, keepdims=True)).max() > 1e-4 * np.abs(J).max()
+    J_bad, _ = _optical_born_currents(dev, n0_lesser_factor=2.0)
+    J_bad_int = J_bad.sum(axis=0) * dE
+    assert np.abs(J_bad_int - J_bad_int.mean()).max() > 1e-3 * np.abs(J_bad_int).max()
