@@ -381,3 +381,23 @@ def test_optical_scba_conserves_energy_integrated_current():
     J_bad, _ = _optical_born_currents(dev, n0_lesser_factor=2.0)
     J_bad_int = J_bad.sum(axis=0) * dE
     assert np.abs(J_bad_int - J_bad_int.mean()).max() > 1e-3 * np.abs(J_bad_int).max()
+
+
+def test_density_sum_rule_fixes_eq7_normalisation():
+    """Eq. (7)'s n_j(E) = Im G^<_jj(E) / 2 pi integrates to the occupation of orbital j.
+
+    Every state of a chain lies in |E| < 2t, and the local density of states A_jj(E) of the
+    open chain integrates to 2 pi (completeness).  With the band filled (mu far above it),
+    integral n_j dE = 1 for every site; at mu = 0, particle-hole symmetry (A(-E) = A(E),
+    f(-E) = 1 - f(E)) gives exactly 1/2.  The substitution E = 2t sin(theta) removes the band-edge
+    singularities of A, so Gauss-Legendre nodes in theta integrate to ~1e-11.
+    """
+    t = 1.0
+    dev = chain_device(5, 0.0, t)
+    x, w = np.polynomial.legendre.leggauss(16)
+    theta, w_theta = 0.5 * np.pi * x, 0.5 * np.pi * w
+    E, wE = 2 * t * np.sin(theta), w_theta * 2 * t * np.cos(theta)
+    for mu, expect in ((10.0, 1.0), (0.0, 0.5)):
+        n = sum(we * O.solve_point(dev.D, dev.T, e, 0.0, None, eta_lead=1e-12, mu_L=mu, mu_R=mu,
+                                   kT=KT)["density"] for e, we in zip(E, wE))
+        assert np.abs(n - expect).max() < 1e-9
