@@ -223,7 +223,10 @@ negf_status negf_integrate(int32_t n_pts, int32_t len, int32_t n_groups, const d
  * 2 = conjugate transpose; op(A) is M x K, op(B) is K x N; strides are in complex elements
  * between batch items (0 = the same matrix for every item; C needs a nonzero stride when
  * n_batch > 1).  FP64 form: CUDA cores.  Mixed form: tensor cores with exact split-BF16
- * slices (error ~2^-45 relative to max|A| max|B| per row and column).  n_batch <= 65535. */
+ * slices (error ~2^-45 relative to max|A| max|B| per row and column), exact for K <= 28032:
+ * a longer mixed-form contraction returns NEGF_ERR_UNSUPPORTED (and a workspace size of 0)
+ * rather than losing accuracy; the same bound applies to the mixed form's block size b in
+ * every other entry point.  n_batch <= 65535. */
 size_t negf_zgemm_workspace_size(int32_t precision, int32_t n_batch, int32_t M, int32_t N,
                                  int32_t K);
 negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, int32_t N,

@@ -483,7 +483,7 @@ extern "C" negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, c
   if (!dev || !opt || dev->n_sys < 1 || dev->n_slabs < 1 || dev->block < 1 || !dev->H_diag ||
       (dev->n_slabs > 1 && !dev->H_up) || n_pts < 0)
     return NEGF_ERR_ARG;
-  if (!engine_supports(opt->precision)) return NEGF_ERR_UNSUPPORTED;
+  if (!engine_supports(opt->precision, dev->block)) return NEGF_ERR_UNSUPPORTED;
   if (!(opt->kT > 0.0) || opt->refine_steps < 0 || opt->refine_steps > 8 || opt->chunk < 0 ||
       opt->adjoint_segment < 0)
     return NEGF_ERR_ARG;

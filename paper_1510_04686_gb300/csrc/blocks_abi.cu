@@ -16,6 +16,7 @@ size_t negf_zgemm_workspace_size(int32_t precision, int32_t n_batch, int32_t M, 
                                  int32_t K) {
   if (!prec_ok(precision) || n_batch < 1 || M < 1 || N < 1 || K < 1) return 0;
   if (precision == NEGF_PREC_FP64) return 256;
+  if (!tc_supports_k(K)) return 0;
   return tc_ws_bytes(n_batch, M, N, K) + 1024;
 }
 
@@ -29,6 +30,7 @@ negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, in
   if (n_batch == 0 || M == 0 || N == 0) return NEGF_OK;
   if (!A || !B || !C || opA < 0 || opA > 2 || opB < 0 || opB > 2) return NEGF_ERR_ARG;
   if (n_batch > 65535) return NEGF_ERR_UNSUPPORTED;
+  if (precision == NEGF_PREC_MIXED && K > 0 && !tc_supports_k(K)) return NEGF_ERR_UNSUPPORTED;
   const int rowsA = opA == OP_N ? M : K, colsA = opA == OP_N ? K : M;
   const int rowsB = opB == OP_N ? K : N, colsB = opB == OP_N ? N : K;
   (void)rowsA;
@@ -60,6 +62,7 @@ negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, in
 
 size_t negf_zinv_workspace_size(int32_t precision, int32_t n_batch, int32_t n) {
   if (!prec_ok(precision) || n_batch < 1 || n < 1) return 0;
+  if (!engine_supports(precision, n)) return 0;
   size_t off = 0;
   EngineWs w;
   carve_engine(nullptr, off, n_batch, n, precision, w);
@@ -73,7 +76,7 @@ negf_status negf_zinv_batched(int32_t precision, int32_t n_batch, int32_t n, dou
     return NEGF_ERR_ARG;
   if (n_batch == 0 || n == 0) return NEGF_OK;
   if (!M || !X || !status) return NEGF_ERR_ARG;
-  if (n_batch > 65535) return NEGF_ERR_UNSUPPORTED;
+  if (n_batch > 65535 || !engine_supports(precision, n)) return NEGF_ERR_UNSUPPORTED;
   if (!ws || ws_bytes < negf_zinv_workspace_size(precision, n_batch, n)) return NEGF_ERR_NOMEM;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (cudaMemsetAsync(status, 0, (size_t)n_batch * sizeof(int32_t), s) != cudaSuccess)

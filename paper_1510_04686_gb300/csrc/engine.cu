@@ -71,8 +71,8 @@ void carve_engine(char* base, size_t& off, int P, int b, int precision, EngineWs
   }
 }
 
-bool engine_supports(int precision) {
-  return precision == NEGF_PREC_FP64 || precision == NEGF_PREC_MIXED;
+bool engine_supports(int precision, int b) {
+  return precision == NEGF_PREC_FP64 || (precision == NEGF_PREC_MIXED && tc_supports_k(b));
 }
 
 static TcWs tc_view(const EngineWs& w, int P, int b) {

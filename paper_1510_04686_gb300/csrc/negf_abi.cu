@@ -417,6 +417,7 @@ const char* negf_status_string(negf_status s) {
 size_t negf_workspace_size(const negf_device* dev, int32_t n_pts, const negf_options* opt,
                            int32_t which) {
   if (!valid_dev(dev) || !valid_opt(opt) || n_pts < 1) return 0;
+  if (!engine_supports(opt->precision, dev->block)) return 0;
   const int b = dev->block, N = dev->n_slabs;
   switch (which) {
     case NEGF_WS_LEAD: return lead_bytes(lead_chunk(dev, n_pts, opt), b, opt);
@@ -431,7 +432,7 @@ negf_status negf_lead_selfenergy(const negf_device* dev, int32_t n_pts, const do
                                  double* sigma_R, double* sigma_L, int32_t* iters,
                                  int32_t* status, void* ws, size_t ws_bytes, void* stream) {
   if (!valid_dev(dev) || !valid_opt(opt) || n_pts < 0) return NEGF_ERR_ARG;
-  if (!engine_supports(opt->precision)) return NEGF_ERR_UNSUPPORTED;
+  if (!engine_supports(opt->precision, dev->block)) return NEGF_ERR_UNSUPPORTED;
   if (n_pts == 0) return NEGF_OK;
   if (!E || !sys_idx || !sigma_R || !sigma_L || !status) return NEGF_ERR_ARG;
   const int b = dev->block;
@@ -462,7 +463,7 @@ negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* 
                            size_t ws_bytes, void* stream) {
   if (!valid_dev(dev) || !valid_opt(opt) || n_pts < 0) return NEGF_ERR_ARG;
   if (scat_R && (e_idx ? n_rows < 1 : n_rows < n_pts)) return NEGF_ERR_ARG;
-  if (!engine_supports(opt->precision)) return NEGF_ERR_UNSUPPORTED;
+  if (!engine_supports(opt->precision, dev->block)) return NEGF_ERR_UNSUPPORTED;
   if (n_pts == 0) return NEGF_OK;
   if (!E || !sys_idx || !sigma_R || !sigma_L || !status) return NEGF_ERR_ARG;
   if ((scat_R == nullptr) != (scat_L == nullptr)) return NEGF_ERR_ARG;

@@ -1170,38 +1170,38 @@ constexpr int kWindowedShape = 6;  // shape 6: (6, 1, 1) with the windowed sched
 constexpr int kNumCfg = 2 * (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 std::atomic<int> g_cfg{18};
 
-void tc_plan(int K, int* beta, int* S, int* parts, int max_parts) {
+bool tc_plan(int K, int* beta, int* S, int* parts, int max_parts) {
   // Slices of beta bits, S = ceil(48 / beta), and the number of K parts such that every group
   // of one order over one part sums to an integer below 2^24 and stays exact in FP32:
-  // 2 Kpart 2^(2 beta) (1 + (S - 2) / 4) <= 2^24.  The widest beta with at most 4 parts wins
-  // (fewest slice products), falling back to narrower digits for very long K.
+  // 2 Kpart 2^(2 beta) (1 + (S - 2) / 4) <= 2^24 (the top digits reach 2^beta, the others
+  // 2^(beta - 1)).  The widest beta whose parts fit max_parts and whose schedule fits the
+  // kernel's item table wins (fewest slice products).  Widths below 4 bits would need more than
+  // kMaxS slices for 48 bits, so a K that no width from 8 down to 4 covers has no exact plan:
+  // false is returned (the placeholder plan must not be launched).
   const int nch = std::max(1, (2 * K + kKC - 1) / kKC);
-  for (int b = 8; b >= 2; --b) {
-    const int s = std::min(kMaxS, (48 + b - 1) / b);
+  for (int b = 8; b >= 4; --b) {
+    const int s = (48 + b - 1) / b;
     const double grow = 1.0 + std::max(0, s - 2) / 4.0;
     const double kmax = 16777216.0 / (std::ldexp(1.0, 2 * b) * grow);  // real terms per part
     const int chunks_per_part = (int)std::floor(kmax / kKC);
     if (chunks_per_part < 1) continue;
     const int np = (nch + chunks_per_part - 1) / chunks_per_part;
-    if (np <= max_parts || b == 2) {
+    if (np <= std::min(max_parts, kMaxParts) && (long long)np * s * (s + 1) / 2 <= kMaxItems) {
       *beta = b;
       *S = s;
-      *parts = std::min(np, kMaxParts);
-      return;
+      *parts = np;
+      return true;
     }
   }
-  *beta = 2;
+  *beta = 4;
   *S = kMaxS;
   *parts = 1;
+  return false;
 }
 
-void tc_plan(int K, int* beta, int* S, int* parts) {
-  tc_plan(K, beta, S, parts, g_cfg.load() % 2 == 0 ? 4 : 8);
-}
-
-void tc_plan(int K, int* beta, int* S) {
-  int parts;
-  tc_plan(K, beta, S, &parts);
+bool tc_supports_k(int K) {
+  int b, s, p;
+  return K >= 1 && tc_plan(K, &b, &s, &p, 4) && tc_plan(K, &b, &s, &p, 8);
 }
 
 template <bool kB>
@@ -1317,7 +1317,8 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
   const int cfg = g_cfg.load();
   const int CG = kShapes[cfg / 2].cg;
   int bta, S, parts;
-  tc_plan(K, &bta, &S, &parts, cfg % 2 == 0 ? 4 : 8);
+  if (!tc_plan(K, &bta, &S, &parts, cfg % 2 == 0 ? 4 : 8))
+    return cudaErrorInvalidValue;  // K beyond the exact range (callers check tc_supports_k)
   const int L = round_up(2 * K, kKC);
   const int N2 = 2 * N;
   __nv_bfloat16* sa = static_cast<__nv_bfloat16*>(ws.slicesA);

@@ -28,10 +28,12 @@ struct TcWs {
 size_t tc_ws_bytes(int P, int M, int N, int K);
 void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, TcWs& w);
 
-// Slices and exactness parameters used for a contraction length K (complex): digit width beta,
-// slice count S and the number of K parts that are accumulated as separate exact groups.
-void tc_plan(int K, int* beta, int* S);
-void tc_plan(int K, int* beta, int* S, int* parts);
+// Slices and exactness parameters for a contraction length K (complex) when at most max_parts
+// K parts may be accumulated as separate exact groups: digit width beta, slice count S
+// (beta S >= 48 bits) and the number of parts.  False when no such plan exists.
+bool tc_plan(int K, int* beta, int* S, int* parts, int max_parts);
+// Whether the tensor-core GEMM covers K exactly under every configuration (K <= 28032).
+bool tc_supports_k(int K);
 
 // The device error word ws.err is set when a bounded wait inside the GEMM kernel gave up (the
 // tile's outputs are then NaN).  tc_timeout_reset zeroes it; tc_timeout_flag ORs

@@ -135,3 +135,37 @@ def test_autotune_cache_rejects_stale_records(tmp_path):
     (tmp_path / "junk.json").write_text("{not json")
     assert autotune.load_cached(str(tmp_path / "junk.json")) is None
     assert autotune.load_cached(str(tmp_path / "missing.json")) is None
+
+
+def test_mixed_form_rejects_contractions_beyond_its_exact_range(lib):
+    """The split-BF16 GEMM keeps 48-bit slices exact for contraction lengths up to 28032; longer
+    ones (blocks, GEMM K, inverse size) are refused on the host instead of losing accuracy."""
+    P = ctypes.c_void_p
+    fake = P(16)
+    mixed, fp64 = B.PREC_MIXED, B.PREC_FP64
+    assert lib.negf_zgemm_workspace_size(mixed, 1, 8, 8, 28032) > 0
+    assert lib.negf_zgemm_workspace_size(mixed, 1, 8, 8, 28033) == 0
+    assert lib.negf_zgemm_workspace_size(fp64, 1, 8, 8, 28033) > 0
+    r = lib.negf_zgemm_batched(mixed, 1, 8, 8, 30000, 1.0, 0.0, fake, 0, 30000, 0, fake, 0, 8, 0,
+                               0.0, 0.0, fake, 64, 8, fake, 1 << 40, None)
+    assert r == 8
+    assert lib.negf_zinv_workspace_size(mixed, 1, 28033) == 0
+    assert lib.negf_zinv_workspace_size(fp64, 1, 28033) > 0
+    r = lib.negf_zinv_batched(mixed, 1, 28033, fake, fake, 2, fake, fake, 1 << 40, None)
+    assert r == 8
+    big = _dev(b=28033)
+    o_mixed = negf.options(precision=mixed)
+    o_fp64 = negf.options(precision=fp64)
+    assert lib.negf_workspace_size(ctypes.byref(big), 1, ctypes.byref(o_mixed), B.WS_RGF) == 0
+    assert lib.negf_workspace_size(ctypes.byref(big), 1, ctypes.byref(o_fp64), B.WS_RGF) > 0
+    r = lib.negf_rgf_solve(ctypes.byref(big), 1, fake, fake, None, fake, fake, None, None, None,
+                           0, ctypes.byref(o_mixed), None, None, None, None, None, fake, fake,
+                           1 << 40, None)
+    assert r == 8
+    r = lib.negf_lead_selfenergy(ctypes.byref(big), 1, fake, fake, ctypes.byref(o_mixed), fake,
+                                 fake, None, fake, fake, 1 << 40, None)
+    assert r == 8
+    # the benchmark's and the adjoint workload's block sizes are inside the range
+    for b in (40, 400, 800, 3430):
+        assert lib.negf_workspace_size(ctypes.byref(_dev(b=b)), 1, ctypes.byref(o_mixed),
+                                       B.WS_RGF) > 0
