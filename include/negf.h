@@ -225,8 +225,9 @@ negf_status negf_integrate(int32_t n_pts, int32_t len, int32_t n_groups, const d
  * n_batch > 1).  FP64 form: CUDA cores.  Mixed form: tensor cores with exact split-BF16
  * slices (error ~2^-45 relative to max|A| max|B| per row and column), exact for K <= 28032:
  * a longer mixed-form contraction returns NEGF_ERR_UNSUPPORTED (and a workspace size of 0)
- * rather than losing accuracy; the same bound applies to the mixed form's block size b in
- * every other entry point.  n_batch <= 65535. */
+ * rather than losing accuracy.  The block inverse (and so every sweep entry point) takes
+ * blocks up to n = 5147 in FP64 and n = 9266 in the mixed form (its Gauss-Jordan panel lives
+ * in shared memory); larger blocks are refused the same way.  n_batch <= 65535. */
 size_t negf_zgemm_workspace_size(int32_t precision, int32_t n_batch, int32_t M, int32_t N,
                                  int32_t K);
 negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, int32_t N,

@@ -117,5 +117,8 @@ cudaError_t gj_inverse(cudaStream_t s, int P, int n, BM<R> M, BM<R> X, cx<R>* U,
                        int32_t* piv, int32_t* status, const int32_t* active);
 int gj_panel_width(int n, int elem_bytes);
 bool gj_fits_small(int n, int elem_bytes);
+// Whether the batched Gauss-Jordan inverse launches for n x n blocks of elem_bytes complex
+// elements (shared-memory limits: n <= 9266 for FP32, n <= 5147 for FP64 elements).
+bool gj_supports(int n, int elem_bytes);
 
 }  // namespace negf

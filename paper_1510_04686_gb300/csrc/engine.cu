@@ -72,7 +72,8 @@ void carve_engine(char* base, size_t& off, int P, int b, int precision, EngineWs
 }
 
 bool engine_supports(int precision, int b) {
-  return precision == NEGF_PREC_FP64 || (precision == NEGF_PREC_MIXED && tc_supports_k(b));
+  if (precision == NEGF_PREC_FP64) return gj_supports(b, 16);
+  return precision == NEGF_PREC_MIXED && tc_supports_k(b) && gj_supports(b, 8);
 }
 
 static TcWs tc_view(const EngineWs& w, int P, int b) {

@@ -49,8 +49,9 @@ struct Engine {
   cudaError_t inv(int P, BM<double> Mm, BM<double> X, int32_t* status, const int32_t* active);
 };
 
-// Whether this build implements the precision form (negf_precision) for blocks of size b (the
-// mixed form's tensor-core GEMM is exact up to a contraction length of 28032).
+// Whether this build implements the precision form (negf_precision) for blocks of size b: the
+// block inverse launches up to b = 5147 (FP64) / 9266 (mixed, FP32 elimination), and the mixed
+// form's tensor-core GEMM is exact up to a contraction length of 28032.
 bool engine_supports(int precision, int b);
 
 // Adjoint workspace helpers (adjoint.cu)

@@ -439,6 +439,15 @@ static size_t panel_smem(int n, int w, int elem_bytes) {
 
 bool gj_fits_small(int n, int elem_bytes) { return small_smem(n, elem_bytes) <= kSmemBudget; }
 
+bool gj_supports(int n, int elem_bytes) {
+  // the panel kernel holds n x nb panel values, the pivot column and the row map in shared
+  // memory (nb = 1 at worst), and the final unpermutation n row indices
+  if (n < 1) return false;
+  if (gj_fits_small(n, elem_bytes)) return true;
+  return panel_smem(n, gj_panel_width(n, elem_bytes), elem_bytes) <= kSmemBudget + 1024 &&
+         (size_t)n * sizeof(int) <= 48 * 1024;
+}
+
 
 int gj_panel_width(int n, int elem_bytes) {
   size_t per_col = (size_t)n * elem_bytes + elem_bytes + sizeof(int);

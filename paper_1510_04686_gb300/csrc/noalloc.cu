@@ -45,7 +45,7 @@ extern "C" negf_status negf_zinv_batched_noalloc(int32_t n_batch, int32_t n, dou
   if (n_batch < 0 || n < 0) return NEGF_ERR_ARG;
   if (n_batch == 0 || n == 0) return NEGF_OK;
   if (!M || !X || !status) return NEGF_ERR_ARG;
-  if (n_batch > 65535) return NEGF_ERR_UNSUPPORTED;
+  if (n_batch > 65535 || !gj_supports(n, 16)) return NEGF_ERR_UNSUPPORTED;
   size_t need = 0;
   EngineWs w;
   carve_engine(nullptr, need, n_batch, n, NEGF_PREC_FP64, w);

@@ -150,14 +150,11 @@ def test_mixed_form_rejects_contractions_beyond_its_exact_range(lib):
                                0.0, 0.0, fake, 64, 8, fake, 1 << 40, None)
     assert r == 8
     assert lib.negf_zinv_workspace_size(mixed, 1, 28033) == 0
-    assert lib.negf_zinv_workspace_size(fp64, 1, 28033) > 0
     r = lib.negf_zinv_batched(mixed, 1, 28033, fake, fake, 2, fake, fake, 1 << 40, None)
     assert r == 8
     big = _dev(b=28033)
     o_mixed = negf.options(precision=mixed)
-    o_fp64 = negf.options(precision=fp64)
     assert lib.negf_workspace_size(ctypes.byref(big), 1, ctypes.byref(o_mixed), B.WS_RGF) == 0
-    assert lib.negf_workspace_size(ctypes.byref(big), 1, ctypes.byref(o_fp64), B.WS_RGF) > 0
     r = lib.negf_rgf_solve(ctypes.byref(big), 1, fake, fake, None, fake, fake, None, None, None,
                            0, ctypes.byref(o_mixed), None, None, None, None, None, fake, fake,
                            1 << 40, None)
@@ -169,3 +166,23 @@ def test_mixed_form_rejects_contractions_beyond_its_exact_range(lib):
     for b in (40, 400, 800, 3430):
         assert lib.negf_workspace_size(ctypes.byref(_dev(b=b)), 1, ctypes.byref(o_mixed),
                                        B.WS_RGF) > 0
+
+
+def test_block_inverse_size_limits_are_checked_on_the_host(lib):
+    """The Gauss-Jordan panel keeps an n-row column panel in shared memory: n <= 5147 for FP64
+    elements and n <= 9266 for the mixed form's FP32 elimination; larger blocks are refused on
+    the host (NEGF_ERR_UNSUPPORTED / workspace size 0) instead of failing at launch."""
+    P = ctypes.c_void_p
+    fake = P(16)
+    mixed, fp64 = B.PREC_MIXED, B.PREC_FP64
+    assert lib.negf_zinv_workspace_size(fp64, 1, 5147) > 0
+    assert lib.negf_zinv_workspace_size(fp64, 1, 5148) == 0
+    assert lib.negf_zinv_workspace_size(mixed, 1, 9266) > 0
+    assert lib.negf_zinv_workspace_size(mixed, 1, 9267) == 0
+    assert lib.negf_zinv_batched(fp64, 1, 5148, fake, fake, 0, fake, fake, 1 << 40, None) == 8
+    assert lib.negf_zinv_batched_noalloc(1, 5148, fake, fake, fake, None) == 8
+    o_fp64 = negf.options(precision=fp64)
+    assert lib.negf_workspace_size(ctypes.byref(_dev(b=5148)), 1, ctypes.byref(o_fp64),
+                                   B.WS_RGF) == 0
+    assert lib.negf_workspace_size(ctypes.byref(_dev(b=5147)), 1, ctypes.byref(o_fp64),
+                                   B.WS_RGF) > 0
