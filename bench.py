@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--points-per-step", type=int, default=256)
-    ap.add_argument("--cpu-points", type=int, default=2)
+    ap.add_argument("--cpu-points", type=int, default=4)
     ap.add_argument("--fp64-points", type=int, default=4)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU-oracle, FP64-GPU and end-to-end side measurements")
