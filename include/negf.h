@@ -22,7 +22,9 @@
  *  - Every array argument is a DEVICE pointer owned by the caller, unless its comment says
  *    "host".  The library never frees or keeps caller memory after a call returns.
  *  - Temporary device memory is the caller's workspace (`ws`, `ws_bytes`), sized by
- *    negf_workspace_size().  The library allocates no device memory of its own.
+ *    negf_workspace_size().  The library allocates no device memory of its own, apart from
+ *    two fixed device arrays reserved on every GPU that loads it: the 32 MiB scratch of
+ *    negf_zinv_batched_noalloc and an 8-byte diagnostic counter.
  *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
  *    Outputs are valid after the stream is synchronised.  Several points are solved
  *    concurrently; the workspace holds a chunk of them at a time.
@@ -43,7 +45,7 @@
 extern "C" {
 #endif
 
-#define NEGF_ABI_VERSION 1
+#define NEGF_ABI_VERSION 2
 
 typedef enum {
   NEGF_OK = 0,
@@ -69,11 +71,24 @@ typedef enum {
                                    point is also NEGF_PT_NONFINITE); set for every point of
                                    the chunk of points that was being solved                */
 
+/* Precision forms.  The mixed forms run every block GEMM on the tensor cores: each row of
+ * op(A) and column of op(B) is scaled by a power of two and rounded once to a fixed-point value
+ * of 40, 48 or 56 bits, cut into exact BF16 slices whose products are summed exactly in FP32
+ * groups; storage, pivoting, norms and reductions stay FP64.  A product's error is about
+ * 2^-bits x K x max|row of A| x max|column of B|.  Issued tensor work per complex product: 15
+ * (40 bits), 28 (48 bits) or 36 (56 bits) slice products for 400 x 400 blocks. */
 typedef enum {
-  NEGF_PREC_FP64 = 0,  /* every block operation in FP64 on the CUDA cores (reference form) */
-  NEGF_PREC_MIXED = 1  /* block GEMMs on the tensor cores as exact split-BF16 slices with
-                          FP32 accumulation, FP64 storage, pivoting, norms and reductions  */
+  NEGF_PREC_FP64 = 0,     /* every block operation in FP64 on the CUDA cores (reference form) */
+  NEGF_PREC_MIXED = 1,    /* tensor cores, 48-bit operand values (the default mixed form)     */
+  NEGF_PREC_MIXED_40 = 2, /* tensor cores, 40-bit operand values (cheaper, less accurate)     */
+  NEGF_PREC_MIXED_56 = 3  /* tensor cores, 56-bit operand values (FP64-class products)        */
 } negf_precision;
+/* negf_options.lead_precision: FP64 when `precision` is FP64, else NEGF_PREC_MIXED_56 (or
+ * NEGF_PREC_MIXED for blocks beyond its exact range, b > 7008).  The
+ * decimation of a lead whose finite segments have near-singular (z - eps) blocks amplifies the
+ * rounding of its early steps by up to ~1e9 (measured on the benchmark device); 56-bit products
+ * keep its error at the level of an FP64 decimation. */
+#define NEGF_PREC_AUTO (-1)
 
 /* Block-tridiagonal device Hamiltonians H(k) of n_sys systems (transverse k x alloy sample).
  * H_diag[s][i]  = H_ii        (Hermitian b x b),  s < n_sys, i < n_slabs
@@ -97,9 +112,9 @@ typedef struct {
   double sr_tol;         /* decimation stop: max(|alpha|_max,|beta|_max) <
                             sr_tol * max(|h|_max, |tau|_max) (default 1e-13)                 */
   int32_t sr_max_iter;   /* decimation iteration cap (default 100)                          */
-  int32_t precision;     /* negf_precision                                                  */
-  int32_t refine_steps;  /* mixed precision: Newton-Schulz steps X <- X + X (I - M X) after
-                            each block inverse (default 2)                                  */
+  int32_t precision;     /* negf_precision of the sweeps (negf_rgf_solve, negf_rgf_adjoint)  */
+  int32_t refine_steps;  /* mixed precision: Newton-Schulz steps X <- X + X (I - M X) run after
+                            every FP32 block inverse (default 2)                            */
   int32_t chunk;         /* points solved concurrently (0 = library default)                */
   int32_t sr_host_check; /* decimation: read the count of unconverged points back every this
                             many steps (after 8) and stop early; 0 = never read back: always run
@@ -107,11 +122,17 @@ typedef struct {
                             call makes no host synchronisation (CUDA-graph capturable).  Default 4 */
   int32_t adjoint_segment; /* negf_rgf_adjoint: slabs per recomputed segment (sweep
                             checkpointing); 0 = keep every slab's blocks.  Default 0 */
+  int32_t lead_precision; /* negf_precision of the lead decimation (negf_lead_selfenergy), or
+                            NEGF_PREC_AUTO (default)                                        */
+  int32_t refine_max;    /* mixed precision: further Newton-Schulz steps, up to refine_max in
+                            all, run only for blocks whose residual max |I - M X| is still
+                            above 2^-24; a block still above it after refine_max steps is
+                            inverted again by FP64 Gauss-Jordan (default 6, range 0-16)      */
 } negf_options;
 
 /* Fill `opt` with the defaults (eta 1e-6 in leads and device, mu_L = +0.1, mu_R = -0.1,
  * kT = 0.025852, sr_tol = 1e-13, sr_max_iter = 100, FP64, refine_steps = 2, chunk = 0,
- * sr_host_check = 4, adjoint_segment = 0). */
+ * sr_host_check = 4, adjoint_segment = 0, lead_precision = NEGF_PREC_AUTO, refine_max = 6). */
 void negf_default_options(negf_options* opt);
 
 int32_t negf_abi_version(void);
@@ -126,11 +147,16 @@ const char* negf_status_string(negf_status s);
  * works through the points `opt->chunk` at a time, so the size saturates). */
 size_t negf_workspace_size(const negf_device* dev, int32_t n_pts, const negf_options* opt,
                            int32_t which);
+/* Block inverses of the mixed forms (on the current device) that were recomputed by FP64
+ * Gauss-Jordan because Newton-Schulz did not reach its residual target within refine_max
+ * steps, since the library was loaded.  Diagnostic; synchronises the device; -1 on error. */
+long long negf_fp64_fallback_count(void);
 
 /* Lead self-energies (Eq. 3, Sigma_lead) by Sancho-Rubio decimation (Lopez Sancho, Lopez
  * Sancho & Rubio, J. Phys. F 15, 851 (1985)); the paper's own leads use the transfer matrix
  * or complex absorbing potential methods (text below Eq. 6), which reach the same unique
- * retarded surface Green's function.
+ * retarded surface Green's function.  Every product and inverse of the decimation runs in
+ * lead_precision (see NEGF_PREC_AUTO); the workspace must be sized with the same options.
  *   E[n_pts]        device double: energy of each point
  *   sys_idx[n_pts]  device int32:  which Hamiltonian of `dev` the point uses (0..n_sys-1)
  *   sigma_R         device complex128 [n_pts][2][b][b] out: Sigma^R of side 0 = left lead
@@ -222,10 +248,12 @@ negf_status negf_integrate(int32_t n_pts, int32_t len, int32_t n_groups, const d
  * block by block as such products).  complex128 row-major; op 0 = none, 1 = transpose,
  * 2 = conjugate transpose; op(A) is M x K, op(B) is K x N; strides are in complex elements
  * between batch items (0 = the same matrix for every item; C needs a nonzero stride when
- * n_batch > 1).  FP64 form: CUDA cores.  Mixed form: tensor cores with exact split-BF16
- * slices (error ~2^-45 relative to max|A| max|B| per row and column), exact for K <= 28032:
- * a longer mixed-form contraction returns NEGF_ERR_UNSUPPORTED (and a workspace size of 0)
- * rather than losing accuracy.  The block inverse (and so every sweep entry point) takes
+ * n_batch > 1).  `precision` is any negf_precision.  FP64 form: CUDA cores.  Mixed forms:
+ * tensor cores with exact split-BF16 slices of 40-, 48- or 56-bit values (error about
+ * 2^-bits x K relative to max|A| max|B| per row and column), exact for K <= 43648
+ * (40 bits), 28032 (48 bits) or 7008 (56 bits): a longer contraction returns
+ * NEGF_ERR_UNSUPPORTED (and a workspace size of 0) rather than losing accuracy.  The block
+ * inverse (and so every sweep entry point) takes
  * blocks up to n = 5147 in FP64 and n = 9266 in the mixed form (its Gauss-Jordan panel lives
  * in shared memory); larger blocks are refused the same way.  n_batch <= 65535. */
 size_t negf_zgemm_workspace_size(int32_t precision, int32_t n_batch, int32_t M, int32_t N,
@@ -241,9 +269,12 @@ negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, in
  * contiguous items.  Gauss-Jordan with partial pivoting (largest |m|^2, lowest row on ties;
  * magnitudes in FP64, or as exact FP32 pairs to about 2^-47 in the mixed form's FP32
  * elimination), pivot reciprocal in the storage precision.
- * FP64 form: FP64 elimination, M is destroyed.  Mixed form: FP32 elimination followed by
- * `refine_steps` Newton-Schulz steps X <- X + X (I - M X) with tensor-core products; M is
- * kept.  status[p] gets NEGF_PT_SINGULAR on an exactly zero pivot. */
+ * FP64 form: FP64 elimination, M is destroyed.  Mixed forms: FP32 elimination followed by
+ * `refine_steps` Newton-Schulz steps X <- X + X (I - M X) with tensor-core products of the
+ * tier's precision, then up to max(refine_steps, 6) steps for blocks whose residual
+ * max |I - M X| is still above 2^-24, and FP64 Gauss-Jordan for blocks still above it (M is
+ * destroyed only by that fallback).  status[p] gets NEGF_PT_SINGULAR on an exactly zero
+ * pivot. */
 size_t negf_zinv_workspace_size(int32_t precision, int32_t n_batch, int32_t n);
 negf_status negf_zinv_batched(int32_t precision, int32_t n_batch, int32_t n, double* M,
                               double* X, int32_t refine_steps, int32_t* status, void* ws,
@@ -257,10 +288,11 @@ negf_status negf_zinv_batched(int32_t precision, int32_t n_batch, int32_t n, dou
  * precision = NEGF_PREC_FP64 and no workspace: the elimination scratch lives in a fixed 32 MiB
  * device array inside this library, reserved on every GPU that loads it until the process
  * exits.  The scratch needed, about n_batch * n * (2 * 16 * nb + 4) bytes with the panel width
- * nb <= 32 (none at all for n up to about 100, which is done in shared memory), must fit those
+ * nb <= 32 (none at all for n <= 106, which is done in shared memory), must fit those
  * 32 MiB, else the call returns NEGF_ERR_NOMEM before launching anything.  The first call on a
  * device looks up the array's device address for that device, with the device current, and
- * keeps it.  Every call on a device shares the one array, which keeps the last call's
+ * keeps it; calls after cudaDeviceReset() on that device are therefore not supported (the
+ * reset may move the array).  Every call on a device shares the one array, which keeps the last call's
  * contents: calls that overlap on the GPU (different streams, or different host threads)
  * race on it and must be serialised by the caller.  It calls no cudaMalloc or cudaFree.
  * M is destroyed; status[p] gets NEGF_PT_SINGULAR on an exactly zero pivot. */

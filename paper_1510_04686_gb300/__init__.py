@@ -32,4 +32,8 @@ from .negf import (  # noqa: F401
     library,
     PREC_FP64,
     PREC_MIXED,
+    PREC_MIXED_40,
+    PREC_MIXED_56,
+    PREC_AUTO,
+    fp64_fallback_count,
 )

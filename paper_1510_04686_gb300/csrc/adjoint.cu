@@ -177,7 +177,8 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   const int seg = adj_segment(a.opt, N);
   const int nseg = (N + seg - 1) / seg;
   carve_adj(wsbase, off, P, b, N, seg, a.opt->precision, w);
-  Engine eng(s, a.opt, w.eng, b, dev->n_sys);
+  Engine eng(s, a.opt->precision, a.opt->refine_steps, refine_limit(a.opt), w.eng, b,
+             dev->n_sys);
   CK(eng.timeout_reset());
   CK(launch_clamp_index(s, P, a.sys, dev->n_sys, w.sys, a.status));
   const int32_t* sysc = w.sys;
@@ -485,7 +486,7 @@ extern "C" negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, c
     return NEGF_ERR_ARG;
   if (!engine_supports(opt->precision, dev->block)) return NEGF_ERR_UNSUPPORTED;
   if (!(opt->kT > 0.0) || opt->refine_steps < 0 || opt->refine_steps > 8 || opt->chunk < 0 ||
-      opt->adjoint_segment < 0)
+      opt->adjoint_segment < 0 || opt->refine_max < 0 || opt->refine_max > 16)
     return NEGF_ERR_ARG;
   if (!V_bar) return NEGF_ERR_ARG;
   const int b = dev->block, N = dev->n_slabs;

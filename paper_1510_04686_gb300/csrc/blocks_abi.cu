@@ -1,23 +1,22 @@
 // Block-level entry points: the batched complex GEMM and block inverse that the sweeps are
 // built from, exposed for callers that assemble their own recursions.
+#include <algorithm>
+
 #include "engine.cuh"
 #include "profile.cuh"
 #include "tc_gemm.cuh"
 
 using namespace negf;
 
-namespace {
-bool prec_ok(int p) { return p == NEGF_PREC_FP64 || p == NEGF_PREC_MIXED; }
-}  // namespace
 
 extern "C" {
 
 size_t negf_zgemm_workspace_size(int32_t precision, int32_t n_batch, int32_t M, int32_t N,
                                  int32_t K) {
-  if (!prec_ok(precision) || n_batch < 1 || M < 1 || N < 1 || K < 1) return 0;
+  if (!prec_valid(precision) || n_batch < 1 || M < 1 || N < 1 || K < 1) return 0;
   if (precision == NEGF_PREC_FP64) return 256;
-  if (!tc_supports_k(K)) return 0;
-  return tc_ws_bytes(n_batch, M, N, K) + 1024;
+  if (!tc_supports_k(K, prec_bits(precision))) return 0;
+  return tc_ws_bytes(n_batch, M, N, K, prec_bits(precision)) + 1024;
 }
 
 negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, int32_t N,
@@ -26,11 +25,12 @@ negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, in
                                int64_t strideB, int32_t ldb, int32_t opB, double beta_re,
                                double beta_im, double* C, int64_t strideC, int32_t ldc,
                                void* ws, size_t ws_bytes, void* stream) {
-  if (!prec_ok(precision) || n_batch < 0 || M < 0 || N < 0 || K < 0) return NEGF_ERR_ARG;
+  if (!prec_valid(precision) || n_batch < 0 || M < 0 || N < 0 || K < 0) return NEGF_ERR_ARG;
   if (n_batch == 0 || M == 0 || N == 0) return NEGF_OK;
   if (!A || !B || !C || opA < 0 || opA > 2 || opB < 0 || opB > 2) return NEGF_ERR_ARG;
   if (n_batch > 65535) return NEGF_ERR_UNSUPPORTED;
-  if (precision == NEGF_PREC_MIXED && K > 0 && !tc_supports_k(K)) return NEGF_ERR_UNSUPPORTED;
+  if (prec_mixed(precision) && K > 0 && !tc_supports_k(K, prec_bits(precision)))
+    return NEGF_ERR_UNSUPPORTED;
   const int rowsA = opA == OP_N ? M : K, colsA = opA == OP_N ? K : M;
   const int rowsB = opB == OP_N ? K : N, colsB = opB == OP_N ? N : K;
   (void)rowsA;
@@ -54,14 +54,16 @@ negf_status negf_zgemm_batched(int32_t precision, int32_t n_batch, int32_t M, in
     size_t off = 0;
     char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
     TcWs tw;
-    tc_ws_carve(base, off, n_batch, M, N, K, tw);
-    e = tc_gemm(s, n_batch, M, N, K, al, a, opA, b, opB, be, c, zero, none, false, nullptr, tw);
+    const int bits = prec_bits(precision);
+    tc_ws_carve(base, off, n_batch, M, N, K, bits, tw);
+    e = tc_gemm(s, n_batch, M, N, K, al, a, opA, b, opB, be, c, zero, none, false, nullptr, tw,
+                bits);
   }
   return note_error(e) == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
 }
 
 size_t negf_zinv_workspace_size(int32_t precision, int32_t n_batch, int32_t n) {
-  if (!prec_ok(precision) || n_batch < 1 || n < 1) return 0;
+  if (!prec_valid(precision) || n_batch < 1 || n < 1) return 0;
   if (!engine_supports(precision, n)) return 0;
   size_t off = 0;
   EngineWs w;
@@ -72,7 +74,7 @@ size_t negf_zinv_workspace_size(int32_t precision, int32_t n_batch, int32_t n) {
 negf_status negf_zinv_batched(int32_t precision, int32_t n_batch, int32_t n, double* M,
                               double* X, int32_t refine_steps, int32_t* status, void* ws,
                               size_t ws_bytes, void* stream) {
-  if (!prec_ok(precision) || n_batch < 0 || n < 0 || refine_steps < 0 || refine_steps > 8)
+  if (!prec_valid(precision) || n_batch < 0 || n < 0 || refine_steps < 0 || refine_steps > 8)
     return NEGF_ERR_ARG;
   if (n_batch == 0 || n == 0) return NEGF_OK;
   if (!M || !X || !status) return NEGF_ERR_ARG;
@@ -87,9 +89,7 @@ negf_status negf_zinv_batched(int32_t precision, int32_t n_batch, int32_t n, dou
   carve_engine(base, off, n_batch, n, precision, w);
   negf_options o;
   negf_default_options(&o);
-  o.precision = precision;
-  o.refine_steps = refine_steps;
-  Engine eng(s, &o, w, n);
+  Engine eng(s, precision, refine_steps, std::max(refine_steps, (int)o.refine_max), w, n);
   const long long nn = (long long)n * n;
   cudaError_t e = eng.timeout_reset();
   if (e == cudaSuccess)

@@ -20,23 +20,45 @@ struct EngineWs {
   cx<float>* invU32;
   cx<float>* invT32;
   z64* r64;          // residual I - M X, P x b x b
-  z64* t64;          // temporary, P x b x b
+  int32_t* act;      // items still refined by the current Newton-Schulz step, P
+  float* rmax;       // max |I - M X| of each item after the last residual product, P
   void* tc;          // tensor-core GEMM operand slices
   size_t tc_bytes;
 };
 
 // Reserve the engine scratch for P concurrent b x b problems at `off` of `base` (base NULL:
-// only advance `off`).
+// only advance `off`).  precision: a negf_precision value (it fixes the tensor-core slices).
 void carve_engine(char* base, size_t& off, int P, int b, int precision, EngineWs& w);
+
+// Precision tiers: FP64 on the CUDA cores, or tensor-core products of 40-, 48- or 56-bit
+// fixed-point operand values.
+inline bool prec_valid(int p) { return p >= NEGF_PREC_FP64 && p <= NEGF_PREC_MIXED_56; }
+inline bool prec_mixed(int p) { return p >= NEGF_PREC_MIXED && p <= NEGF_PREC_MIXED_56; }
+inline int prec_bits(int p) {
+  return p == NEGF_PREC_MIXED ? 48 : p == NEGF_PREC_MIXED_40 ? 40 : p == NEGF_PREC_MIXED_56 ? 56 : 0;
+}
+// Precision of the lead decimation of b x b blocks under options o (NEGF_PREC_AUTO: FP64 when
+// the sweeps are FP64, else the 56-bit tier where its products are exact (b <= 7008), else the
+// 48-bit tier).
+int lead_precision(const negf_options* o, int b);
+// Newton-Schulz steps of the mixed-form inverse: always refine_steps, at most
+// max(refine_steps, refine_max).
+inline int refine_limit(const negf_options* o) {
+  return o->refine_max > o->refine_steps ? o->refine_max : o->refine_steps;
+}
 
 struct Engine {
   cudaStream_t s;
-  const negf_options* opt;
+  int prec;        // negf_precision of every product and inverse of this engine
+  int refine_min;  // mixed form: Newton-Schulz steps run for every block
+  int refine_max;  // ... and at most this many for blocks whose residual stays above 2^-24
   EngineWs w;
   int b;
   int n_sys = 0;  // distinct Hamiltonians an indexed operand selects from (0 = unknown)
-  Engine(cudaStream_t s_, const negf_options* o, const EngineWs& w_, int b_, int n_sys_ = 0)
-      : s(s_), opt(o), w(w_), b(b_), n_sys(n_sys_) {}
+  Engine(cudaStream_t s_, int prec_, int rmin, int rmax_, const EngineWs& w_, int b_,
+         int n_sys_ = 0)
+      : s(s_), prec(prec_), refine_min(rmin), refine_max(rmax_ > rmin ? rmax_ : rmin), w(w_),
+        b(b_), n_sys(n_sys_) {}
   // C = alpha op(A) op(B) + beta C + gamma D for P batch items of M x N x K.
   cudaError_t gemm(int P, int M, int N, int K, z64 alpha, BMc<double> A, int opA, BMc<double> B,
                    int opB, z64 beta, BM<double> C, z64 gamma, BMc<double> D,
@@ -46,12 +68,20 @@ struct Engine {
   cudaError_t timeout_reset();
   cudaError_t timeout_flag(int P, int32_t* status);
   // X = Mm^-1 for P items of size b (Mm is destroyed); zero pivots flag status[item].
+  // Mixed form: FP32 Gauss-Jordan start, refine_min Newton-Schulz steps for every item, further
+  // steps (up to refine_max) only for items whose residual max |I - M X| is still above 2^-24,
+  // and an FP64 Gauss-Jordan inverse for the items still above it after refine_max steps.
   cudaError_t inv(int P, BM<double> Mm, BM<double> X, int32_t* status, const int32_t* active);
 };
 
+// Number of block inverses (on the current device) that the mixed form recomputed in FP64
+// because Newton-Schulz did not reach its residual target (synchronises the device).
+long long engine_fp64_fallbacks();
+
 // Whether this build implements the precision form (negf_precision) for blocks of size b: the
 // block inverse launches up to b = 5147 (FP64) / 9266 (mixed, FP32 elimination), and the mixed
-// form's tensor-core GEMM is exact up to a contraction length of 28032.
+// form's tensor-core GEMM is exact up to a contraction length that depends on the tier (48-bit
+// values: 28032).
 bool engine_supports(int precision, int b);
 
 // Adjoint workspace helpers (adjoint.cu)

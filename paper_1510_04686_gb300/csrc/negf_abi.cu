@@ -46,8 +46,10 @@ bool valid_opt(const negf_options* o) {
   if (!o) return false;
   if (!(o->eta_lead >= 0.0) || !(o->eta_device >= 0.0) || !(o->kT > 0.0)) return false;
   if (!(o->sr_tol > 0.0) || o->sr_max_iter < 1 || o->sr_max_iter > 100000) return false;
-  if (o->precision != NEGF_PREC_FP64 && o->precision != NEGF_PREC_MIXED) return false;
+  if (!prec_valid(o->precision)) return false;
+  if (o->lead_precision != NEGF_PREC_AUTO && !prec_valid(o->lead_precision)) return false;
   if (o->refine_steps < 0 || o->refine_steps > 8 || o->chunk < 0) return false;
+  if (o->refine_max < 0 || o->refine_max > 16) return false;
   if (o->sr_host_check < 0 || o->adjoint_segment < 0) return false;
   return true;
 }
@@ -79,7 +81,7 @@ void carve_lead(Carver& c, int P, int b, const negf_options* opt, LeadWs& w) {
   w.item_status = c.take<int32_t>(Q);
   w.n_active = c.take<int32_t>(1);
   w.sys = c.take<int32_t>((size_t)P);
-  carve_engine(c.base ? c.base : nullptr, c.off, (int)Q, b, opt->precision, w.eng);
+  carve_engine(c.base ? c.base : nullptr, c.off, (int)Q, b, lead_precision(opt, b), w.eng);
 }
 
 struct RgfWs {
@@ -161,7 +163,8 @@ negf_status lead_chunk_run(const negf_device* dev, int P, const double* E, const
   Carver c{wsbase, 0};
   LeadWs w;
   carve_lead(c, P, b, opt, w);
-  Engine eng(s, opt, w.eng, b, dev->n_sys);
+  Engine eng(s, lead_precision(opt, b), opt->refine_steps, refine_limit(opt), w.eng, b,
+             dev->n_sys);
   CK(eng.timeout_reset());
   CK(launch_clamp_index(s, P, sys_in, dev->n_sys, w.sys, status));
   const int32_t* sys = w.sys;
@@ -258,7 +261,8 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
   Carver c{wsbase, 0};
   RgfWs w;
   carve_rgf(c, P, b, N, a.opt, w);
-  Engine eng(s, a.opt, w.eng, b, dev->n_sys);
+  Engine eng(s, a.opt->precision, a.opt->refine_steps, refine_limit(a.opt), w.eng, b,
+             dev->n_sys);
   CK(eng.timeout_reset());
   const double eta = a.opt->eta_device;
   CK(launch_clamp_index(s, P, a.sys, dev->n_sys, w.sys, a.status));
@@ -395,9 +399,13 @@ void negf_default_options(negf_options* o) {
   o->chunk = 0;
   o->sr_host_check = 4;
   o->adjoint_segment = 0;
+  o->lead_precision = NEGF_PREC_AUTO;
+  o->refine_max = 6;
 }
 
 int32_t negf_abi_version(void) { return NEGF_ABI_VERSION; }
+
+long long negf_fp64_fallback_count(void) { return engine_fp64_fallbacks(); }
 
 const char* negf_status_string(negf_status s) {
   switch (s) {
@@ -417,7 +425,9 @@ const char* negf_status_string(negf_status s) {
 size_t negf_workspace_size(const negf_device* dev, int32_t n_pts, const negf_options* opt,
                            int32_t which) {
   if (!valid_dev(dev) || !valid_opt(opt) || n_pts < 1) return 0;
-  if (!engine_supports(opt->precision, dev->block)) return 0;
+  if (which == NEGF_WS_LEAD ? !engine_supports(lead_precision(opt, dev->block), dev->block)
+                            : !engine_supports(opt->precision, dev->block))
+    return 0;
   const int b = dev->block, N = dev->n_slabs;
   switch (which) {
     case NEGF_WS_LEAD: return lead_bytes(lead_chunk(dev, n_pts, opt), b, opt);
@@ -432,7 +442,7 @@ negf_status negf_lead_selfenergy(const negf_device* dev, int32_t n_pts, const do
                                  double* sigma_R, double* sigma_L, int32_t* iters,
                                  int32_t* status, void* ws, size_t ws_bytes, void* stream) {
   if (!valid_dev(dev) || !valid_opt(opt) || n_pts < 0) return NEGF_ERR_ARG;
-  if (!engine_supports(opt->precision, dev->block)) return NEGF_ERR_UNSUPPORTED;
+  if (!engine_supports(lead_precision(opt, dev->block), dev->block)) return NEGF_ERR_UNSUPPORTED;
   if (n_pts == 0) return NEGF_OK;
   if (!E || !sys_idx || !sigma_R || !sigma_L || !status) return NEGF_ERR_ARG;
   const int b = dev->block;

@@ -18,7 +18,9 @@ std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device (looked up once per device: in
-// host code the array's name is only a host-side stand-in, not a device address).
+// host code the array's name is only a host-side stand-in, not a device address).  The cached
+// address belongs to the device context of the first call; after cudaDeviceReset the module is
+// loaded again, possibly elsewhere, so calls after a reset are not supported.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -46,9 +48,10 @@ extern "C" negf_status negf_zinv_batched_noalloc(int32_t n_batch, int32_t n, dou
   if (n_batch == 0 || n == 0) return NEGF_OK;
   if (!M || !X || !status) return NEGF_ERR_ARG;
   if (n_batch > 65535 || !gj_supports(n, 16)) return NEGF_ERR_UNSUPPORTED;
+  // blocks small enough for the one-CTA shared-memory elimination use no scratch at all
   size_t need = 0;
   EngineWs w;
-  carve_engine(nullptr, need, n_batch, n, NEGF_PREC_FP64, w);
+  if (!gj_fits_small(n, (int)sizeof(z64))) carve_engine(nullptr, need, n_batch, n, NEGF_PREC_FP64, w);
   if (need > kNoAllocBytes) return NEGF_ERR_NOMEM;
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return NEGF_ERR_CUDA;

@@ -13,6 +13,7 @@
 
 #include "profile.cuh"
 #include "tc_gemm.cuh"
+#include "tc_slice.cuh"
 
 namespace negf {
 namespace {
@@ -175,325 +176,9 @@ __device__ __forceinline__ double f32_scaled(uint32_t xb, int k) {
 }
 
 
-// ------------------------------------------------------------------ slicing kernels
-template <typename T>
-__device__ __forceinline__ T warp_max(T v) {
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+__device__ __forceinline__ float warp_max_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
-}
-
-
-// |x| as an ordered integer (the bit pattern without the sign)
-__device__ __forceinline__ unsigned long long absbits(double x) {
-  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-}
-
-// exponent e with max|x| < 2^e (0 for an all-zero row)
-__device__ __forceinline__ int scale_exp(double mx) {
-  if (!(mx > 0.0)) return 0;
-  int e;
-  frexp(mx, &e);
-  return e;
-}
-
-// Fixed-point slicing of one value.  x 2^(beta - e) (|x| < 2^e) is rounded once to the integer
-// R = round(|x| 2^(beta S - e)) < 2^(beta S) + 1 and written in balanced base-2^beta digits
-// q_0 .. q_{S-1} (value sum_s q_s 2^(-beta s)): q_0 in [0, 2^beta], q_s in [-2^(beta-1),
-// 2^(beta-1)) for s >= 1.  Adding H = 2^(beta-1) to every digit position below the top one turns
-// the balanced digits into plain bit fields of R + H (minus 2^(beta-1)), so each digit is a
-// constant shift and mask.  Every q_s 2^(-beta s) is exact in BF16.
-template <int BETA, int S>
-struct Digits {
-  static constexpr int kBits = BETA * S;
-  static_assert(kBits <= 56, "fixed-point value must fit 64 bits with headroom");
-  static constexpr unsigned long long kH = [] {
-    unsigned long long h = 0;
-    for (int s = 1; s < S; ++s) h |= (1ull << (BETA - 1)) << (BETA * (S - 1 - s));
-    return h;
-  }();
-};
-
-// R + H for |x| with line exponent e, and the sign of x.
-template <int BETA, int S>
-__device__ __forceinline__ unsigned long long fixed_point(double x, int e, bool& neg) {
-  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  neg = (u >> 63) != 0;
-  const int ex = (int)((u >> 52) & 0x7FF);
-  unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
-  if (ex) mant |= 1ull << 52;
-  const int sh = (ex ? ex : 1) - 1075 + Digits<BETA, S>::kBits - e;  // |x| 2^(beta S - e) = mant 2^sh
-  unsigned long long R;
-  if (mant == 0 || sh <= -64) {
-    R = 0;
-  } else if (sh >= 0) {
-    R = mant << sh;
-  } else {
-    const int r = -sh;
-    R = (mant + (1ull << (r - 1))) >> r;
-  }
-  return R + Digits<BETA, S>::kH;
-}
-
-// Slice s of a value from its R + H: sign * q_s * 2^(-beta s) as FP32 (exact).
-template <int BETA, int S, int SI>
-__device__ __forceinline__ float digit(unsigned long long RH, bool neg) {
-  constexpr int pos = BETA * (S - 1 - SI);
-  int q = (SI == 0) ? (int)(RH >> pos) : (int)((RH >> pos) & ((1ull << BETA) - 1)) - (1 << (BETA - 1));
-  // |q| <= 2^8: exact through the 1.5 * 2^23 bias
-  float f = __int_as_float(0x4B400000 + q) - 12582912.0f;
-  f *= __int_as_float((127 - BETA * SI) << 23);  // 2^(-beta s)
-  return neg ? -f : f;
-}
-
-constexpr int kTK = 32;  // complex K values per tile
-constexpr int kMaxS = 12;
-
-template <int S>
-struct Unroll {
-  template <class F>
-  __device__ __forceinline__ static void run(F&& f) {
-    Unroll<S - 1>::run(f);
-    f(std::integral_constant<int, S - 1>{});
-  }
-};
-template <>
-struct Unroll<0> {
-  template <class F>
-  __device__ __forceinline__ static void run(F&&) {}
-};
-
-// Slicing of 32 "lines" per CTA (rows of op(A), or columns of op(B)).  Pass 1 finds each line's
-// scale exponent with coalesced reads along the line's memory layout; pass 2 walks 32 x 32
-// complex tiles through shared memory (so a line that is a column in memory costs the same as a
-// row) and writes the S slices with 16-byte stores.  A lines become one output row
-// [Re, Im, Re, Im, ...]; B lines (columns n of op(B)) become the two rows 2n = [Re, -Im, ...]
-// and 2n + 1 = [Im, Re, ...] of the real embedding.  Padding columns up to L are written as 0.
-template <bool kB, int BETA, int S>
-__global__ void __launch_bounds__(256) k_slice(int n_lines, int K, int L, BMc<double> X, int op,
-                                               bool line_is_col, __nv_bfloat16* out,
-                                               int32_t* eo, const int32_t* active) {
-  const int p = blockIdx.y;
-  if (active && !active[p]) return;
-  __shared__ z64 tile[32][kTK + 1];
-  __shared__ unsigned long long smax[8][32];
-  __shared__ int sexp[32];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int l0 = blockIdx.x * 32;
-  const z64* x = bat(X, p);
-  const long long ld = X.ld;
-  const bool conj = (op == OP_C);
-
-  // ---- pass 1: max |Re|, |Im| over each line (bit patterns compare as magnitudes)
-  if (!line_is_col) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int li = w + 8 * j, line = l0 + li;
-      unsigned long long m = 0;
-      if (line < n_lines) {
-        const z64* row = x + (long long)line * ld;
-        for (int k = lane; k < K; k += 32) {
-          const z64 v = row[k];
-          m = max(m, max(absbits(v.re), absbits(v.im)));
-        }
-      }
-      m = warp_max(m);
-      if (lane == 0) smax[0][li] = m;
-    }
-  } else {
-    const int line = l0 + lane;
-    unsigned long long m = 0;
-    if (line < n_lines)
-      for (int k = w; k < K; k += 8) {
-        const z64 v = x[(long long)k * ld + line];
-        m = max(m, max(absbits(v.re), absbits(v.im)));
-      }
-    smax[w][lane] = m;
-    __syncthreads();
-    if (w == 0) {
-      unsigned long long mm = smax[0][lane];
-#pragma unroll
-      for (int i = 1; i < 8; ++i) mm = max(mm, smax[i][lane]);
-      smax[0][lane] = mm;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int li = threadIdx.x, line = l0 + li;
-    const int e = scale_exp(__longlong_as_double((long long)smax[0][li]));
-    sexp[li] = e;
-    if (line < n_lines) eo[(long long)p * n_lines + line] = e;
-  }
-  __syncthreads();
-
-  // ---- pass 2: tiles of 32 lines x 32 complex K values.  Thread (li, g) converts the four
-  // values k = 4g .. 4g + 3 of line li; lanes 0-7 of a quarter-warp hold eight different lines
-  // (conflict-free shared-memory reads), and the four quarter-warps cover 16 consecutive k.
-  const int li = (w & 3) * 8 + (lane & 7);
-  const int g = (w >> 2) * 4 + (lane >> 3);
-  const int line = l0 + li;
-  const int e = sexp[li];
-  const long long rows_out = kB ? 2LL * n_lines : (long long)n_lines;
-  for (int k0 = 0; k0 < L / 2; k0 += kTK) {
-    if (k0 < K) {
-      for (int t = threadIdx.x; t < 32 * kTK; t += 256) {
-        const int a = t >> 5, c = t & 31;  // a: slow index, c: fast (contiguous) index
-        int tl, tk;
-        if (line_is_col) {
-          tk = a;
-          tl = c;  // memory x[k][line]
-        } else {
-          tl = a;
-          tk = c;  // memory x[line][k]
-        }
-        const int ln = l0 + tl, kk = k0 + tk;
-        z64 v = mkc(0.0, 0.0);
-        if (ln < n_lines && kk < K)
-          v = line_is_col ? x[(long long)kk * ld + ln] : x[(long long)ln * ld + kk];
-        tile[tl][tk] = v;
-      }
-    }
-    __syncthreads();
-    if (line < n_lines) {
-      unsigned long long rr[4], ri[4];
-      bool nr[4], ni[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        z64 v = (k0 < K) ? tile[li][4 * g + j] : mkc(0.0, 0.0);
-        if (conj) v.im = -v.im;
-        rr[j] = fixed_point<BETA, S>(v.re, e, nr[j]);
-        ri[j] = fixed_point<BETA, S>(v.im, e, ni[j]);
-      }
-      const long long col = 2LL * (k0 + 4 * g);  // first BF16 column of this thread's 4 values
-      Unroll<S>::run([&](auto sc) {
-        constexpr int s = decltype(sc)::value;
-        __nv_bfloat16* base = out + ((long long)p * S + s) * rows_out * L;
-        uint32_t w0[4], w1[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float fr = digit<BETA, S, s>(rr[j], nr[j]);
-          const float fi = digit<BETA, S, s>(ri[j], ni[j]);
-          __nv_bfloat162 a, b2;
-          if (!kB) {
-            a = __floats2bfloat162_rn(fr, fi);
-          } else {
-            a = __floats2bfloat162_rn(fr, -fi);
-            b2 = __floats2bfloat162_rn(fi, fr);
-            w1[j] = *reinterpret_cast<uint32_t*>(&b2);
-          }
-          w0[j] = *reinterpret_cast<uint32_t*>(&a);
-        }
-        if (!kB) {
-          *reinterpret_cast<uint4*>(base + (long long)line * L + col) =
-              make_uint4(w0[0], w0[1], w0[2], w0[3]);
-        } else {
-          *reinterpret_cast<uint4*>(base + (2LL * line) * L + col) =
-              make_uint4(w0[0], w0[1], w0[2], w0[3]);
-          *reinterpret_cast<uint4*>(base + (2LL * line + 1) * L + col) =
-              make_uint4(w1[0], w1[1], w1[2], w1[3]);
-        }
-      });
-    }
-    __syncthreads();
-  }
-}
-
-// Slicing of 8 lines per CTA with the whole strip (8 lines x K complex values) held in shared
-// memory: the operand is read from memory once (the exponent pass and the digit pass both read
-// the strip), and each lane converts one complex value, so every slice store of a warp is one
-// contiguous 128-byte row segment.  Used when the strip fits (K up to kStripMaxK).
-constexpr int kStripLines = 8;
-constexpr int kStripMaxK = 858;  // 8 x (K + 1) x 16 B <= 110 KB: two CTAs per SM
-template <bool kB, int BETA, int S>
-__global__ void __launch_bounds__(256) k_slice_strip(int n_lines, int K, int L, BMc<double> X,
-                                                     int op, bool line_is_col,
-                                                     __nv_bfloat16* out, int32_t* eo,
-                                                     const int32_t* active) {
-  const int p = blockIdx.y;
-  if (active && !active[p]) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  z64* strip = reinterpret_cast<z64*>(smem_raw);  // [kStripLines][K + 1] (padded rows)
-  __shared__ int sexp[kStripLines];
-  const int lds = K + 1;
-  const int l0 = blockIdx.x * kStripLines;
-  const z64* x = bat(X, p);
-  const long long ld = X.ld;
-  const bool conj = (op == OP_C);
-  const z64 zero = mkc(0.0, 0.0);
-  // load the strip along the operand's memory layout (coalesced either way): element e is
-  // (line e / K, k = e % K) for row lines and (line e % 8, k = e / 8) for column lines; eight
-  // loads per thread are in flight before their shared-memory stores
-  const int tot = kStripLines * K;
-  for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * 256) {
-    z64 v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * 256;
-      v[u] = zero;
-      if (e < tot) {
-        const int li = line_is_col ? (e & (kStripLines - 1)) : e / K;
-        const int k = line_is_col ? e / kStripLines : e - li * K;
-        const int line = l0 + li;
-        if (line < n_lines)
-          v[u] = line_is_col ? x[(long long)k * ld + line] : x[(long long)line * ld + k];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * 256;
-      if (e < tot) {
-        const int li = line_is_col ? (e & (kStripLines - 1)) : e / K;
-        const int k = line_is_col ? e / kStripLines : e - li * K;
-        z64 w = v[u];
-        if (conj) w.im = -w.im;
-        strip[li * lds + k] = w;
-      }
-    }
-  }
-  __syncthreads();
-  {  // scale exponent of each line: warp w reduces line w
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w < kStripLines) {
-      unsigned long long m = 0;
-      for (int k = lane; k < K; k += 32) {
-        const z64 v = strip[w * lds + k];
-        m = max(m, max(absbits(v.re), absbits(v.im)));
-      }
-      m = warp_max(m);
-      if (lane == 0) {
-        const int e = scale_exp(__longlong_as_double((long long)m));
-        sexp[w] = e;
-        if (l0 + w < n_lines) eo[(long long)p * n_lines + l0 + w] = e;
-      }
-    }
-  }
-  __syncthreads();
-  const long long rows_out = kB ? 2LL * n_lines : (long long)n_lines;
-  for (int li = 0; li < kStripLines; ++li) {
-    const int line = l0 + li;
-    if (line >= n_lines) break;
-    const int e = sexp[li];
-    for (int k = threadIdx.x; k < L / 2; k += blockDim.x) {
-      const z64 v = k < K ? strip[li * lds + k] : zero;
-      bool nr, ni;
-      const unsigned long long rr = fixed_point<BETA, S>(v.re, e, nr);
-      const unsigned long long ri = fixed_point<BETA, S>(v.im, e, ni);
-      Unroll<S>::run([&](auto sc) {
-        constexpr int sl = decltype(sc)::value;
-        const float fr = digit<BETA, S, sl>(rr, nr);
-        const float fi = digit<BETA, S, sl>(ri, ni);
-        __nv_bfloat16* base = out + ((long long)p * S + sl) * rows_out * L;
-        if (!kB) {
-          reinterpret_cast<__nv_bfloat162*>(base + (long long)line * L)[k] =
-              __floats2bfloat162_rn(fr, fi);
-        } else {
-          reinterpret_cast<__nv_bfloat162*>(base + (2LL * line) * L)[k] =
-              __floats2bfloat162_rn(fr, -fi);
-          reinterpret_cast<__nv_bfloat162*>(base + (2LL * line + 1) * L)[k] =
-              __floats2bfloat162_rn(fi, fr);
-        }
-      });
-    }
-  }
 }
 
 // ------------------------------------------------------------------ MMA kernel
@@ -581,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int32_t* __restrict__ zidxA, int zmodeA, const int32_t* __restrict__ zidxB,
               int zmodeB, z64 alpha,
               z64 beta, z64 gamma, BM<double> C, BMc<double> D, int add_identity,
-              int trunc_beta, const int32_t* active, int32_t* err) {
+              int trunc_beta, const int32_t* active, int32_t* err, float* rmax) {
   static_assert(NT * (kAccBufs + 2) == 512, "TMEM: kAccBufs accumulators + hi / lo sum words");
   static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair per MMA");
   static_assert(!WIN || (CG == 1 && G == 1), "windowed schedule: one CTA, one stage per commit");
@@ -927,6 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int cbase = half * (NT / 2);
     const uint32_t t_hi = tmem + lane_off + kAccBufs * NT, t_lo = t_hi + NT;
     const int n_exec = (sched.n_acc / S) * min(cut, S);  // groups of orders <= cut per part
+    float omax = 0.0f;  // largest |Re|, |Im| this thread stores (for rmax)
     for (int acc = 0; acc < n_exec; ++acc) {
       const int buf = acc % kAccBufs;
       if (!mbar_wait(&accfull[buf], (acc / kAccBufs) & 1, abort_flag)) break;
@@ -993,6 +679,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (add_identity && n == mr) o.re += 1.0;
                 *cp = o;
+                omax = fmaxf(omax, (float)fmax(fabs(o.re), fabs(o.im)));
               }
             }
             __syncwarp();
@@ -1008,6 +695,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         else
           mbar_arrive(&accempty[buf]);
       }
+    }
+    if (rmax) {  // per-item max |output| (non-negative floats order like their bit patterns)
+      const float wm = warp_max_f(omax);
+      if (lane == 0 && wm > 0.0f)
+        atomicMax(reinterpret_cast<unsigned int*>(rmax + p), __float_as_uint(wm));
     }
     if (*abort_flag && row_ok) {
       // a bounded wait gave up: this tile's outputs are NaN, so that the caller's finite checks
@@ -1092,25 +784,13 @@ Sched build_sched(int S, int n_chunks, int n_parts) {
   return sc;
 }
 
-// Kernel attributes (the dynamic shared-memory limit) belong to a device context, so each
-// kernel records, per device (ordinals below 32), whether it has set them there.
-static cudaError_t set_smem_once(std::atomic<unsigned>& done, const void* fn, int bytes) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  const unsigned bit = 1u << (dev & 31);
-  if (done.load() & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) done.fetch_or(bit);
-  return e;
-}
 
 template <int NT, int STAGES, int CG, int G, bool WIN = false, int KPS = 1>
 cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S, int two_beta,
                       int n_parts, const CUtensorMap& mA, const CUtensorMap& mB, const TcWs& ws,
                       const int32_t* zA, int zmA, const int32_t* zB, int zmB, z64 alpha,
                       z64 beta, z64 gamma, BM<double> C, BMc<double> D, bool add_identity,
-                      int trunc_beta, const int32_t* active) {
+                      int trunc_beta, const int32_t* active, float* rmax) {
   using CF = Cfg<NT, STAGES, CG, G, KPS>;
   static std::atomic<unsigned> attr{0};
   {
@@ -1146,7 +826,7 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
   cudaError_t e = cudaLaunchKernelEx(&lc, k_tc_gemm<NT, STAGES, CG, G, WIN, KPS>, mA, mB, sc, M, N2, S,
                                      two_beta, (const int32_t*)ws.expA, (const int32_t*)ws.expB,
                                      zA, zmA, zB, zmB, alpha, beta, gamma, C, D,
-                                     add_identity ? 1 : 0, trunc_beta, active, ws.err);
+                                     add_identity ? 1 : 0, trunc_beta, active, ws.err, rmax);
   prof_end(s, PROF_TC_GEMM);
   count_launch();
   if (e != cudaSuccess) return e;
@@ -1170,27 +850,31 @@ constexpr int kWindowedShape = 6;  // shape 6: (6, 1, 1) with the windowed sched
 constexpr int kNumCfg = 2 * (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 std::atomic<int> g_cfg{18};
 
-bool tc_plan(int K, int* beta, int* S, int* parts, int max_parts) {
-  // Slices of beta bits, S = ceil(48 / beta), and the number of K parts such that every group
-  // of one order over one part sums to an integer below 2^24 and stays exact in FP32:
-  // 2 Kpart 2^(2 beta) (1 + (S - 2) / 4) <= 2^24 (the top digits reach 2^beta, the others
-  // 2^(beta - 1)).  The widest beta whose parts fit max_parts and whose schedule fits the
-  // kernel's item table wins (fewest slice products).  Widths below 4 bits would need more than
-  // kMaxS slices for 48 bits, so a K that no width from 8 down to 4 covers has no exact plan:
-  // false is returned (the placeholder plan must not be launched).
+bool tc_bits_ok(int bits) { return bits == 40 || bits == 48 || bits == 56; }
+
+bool tc_plan(int K, int bits, int* beta, int* S, int* parts, int max_parts) {
+  // Slices of beta bits, S = ceil(bits / beta) (beta S <= 60, S <= kMaxS), and the number of K
+  // parts such that every group of one order over one part sums to an integer below 2^24 and
+  // stays exact in FP32: 2 Kpart 2^(2 beta) (1 + (S - 2) / 4) <= 2^24 (the top digits reach
+  // 2^beta, the others 2^(beta - 1)).  The widest beta whose parts fit max_parts and whose
+  // schedule fits the kernel's item table wins (fewest slice products).  When no width from 8
+  // down to 4 covers K, false is returned (the placeholder plan must not be launched).
   const int nch = std::max(1, (2 * K + kKC - 1) / kKC);
-  for (int b = 8; b >= 4; --b) {
-    const int s = (48 + b - 1) / b;
-    const double grow = 1.0 + std::max(0, s - 2) / 4.0;
-    const double kmax = 16777216.0 / (std::ldexp(1.0, 2 * b) * grow);  // real terms per part
-    const int chunks_per_part = (int)std::floor(kmax / kKC);
-    if (chunks_per_part < 1) continue;
-    const int np = (nch + chunks_per_part - 1) / chunks_per_part;
-    if (np <= std::min(max_parts, kMaxParts) && (long long)np * s * (s + 1) / 2 <= kMaxItems) {
-      *beta = b;
-      *S = s;
-      *parts = np;
-      return true;
+  if (tc_bits_ok(bits)) {
+    for (int b = 8; b >= 4; --b) {
+      const int s = (bits + b - 1) / b;
+      if (s > kMaxS || b * s > 60) continue;
+      const double grow = 1.0 + std::max(0, s - 2) / 4.0;
+      const double kmax = 16777216.0 / (std::ldexp(1.0, 2 * b) * grow);  // real terms per part
+      const int chunks_per_part = (int)std::floor(kmax / kKC);
+      if (chunks_per_part < 1) continue;
+      const int np = (nch + chunks_per_part - 1) / chunks_per_part;
+      if (np <= std::min(max_parts, kMaxParts) && (long long)np * s * (s + 1) / 2 <= kMaxItems) {
+        *beta = b;
+        *S = s;
+        *parts = np;
+        return true;
+      }
     }
   }
   *beta = 4;
@@ -1199,45 +883,11 @@ bool tc_plan(int K, int* beta, int* S, int* parts, int max_parts) {
   return false;
 }
 
-bool tc_supports_k(int K) {
+bool tc_supports_k(int K, int bits) {
   int b, s, p;
-  return K >= 1 && tc_plan(K, &b, &s, &p, 4) && tc_plan(K, &b, &s, &p, 8);
+  return K >= 1 && tc_plan(K, bits, &b, &s, &p, 4) && tc_plan(K, bits, &b, &s, &p, 8);
 }
 
-template <bool kB>
-cudaError_t launch_slice(cudaStream_t s, int beta, int S, dim3 grid, int n_lines, int K, int L,
-                         BMc<double> X, int op, bool line_is_col, __nv_bfloat16* out, int32_t* eo,
-                         const int32_t* active) {
-  const bool strip = K <= kStripMaxK;
-  const size_t strip_smem = (size_t)kStripLines * (K + 1) * sizeof(z64);
-  const dim3 sgrid((n_lines + kStripLines - 1) / kStripLines, grid.y);
-#define NEGF_SLICE_CASE(B_, S_)                                                             \
-  if (beta == B_ && S == S_) {                                                              \
-    if (strip) {                                                                            \
-      static std::atomic<unsigned> attr{0};                                                 \
-      cudaError_t ea = set_smem_once(                                                       \
-          attr, reinterpret_cast<const void*>(&k_slice_strip<kB, B_, S_>),                  \
-          kStripLines * (kStripMaxK + 1) * 16);                                             \
-      if (ea != cudaSuccess) return ea;                                                     \
-      k_slice_strip<kB, B_, S_><<<sgrid, 256, strip_smem, s>>>(n_lines, K, L, X, op,        \
-                                                                line_is_col, out, eo,       \
-                                                                active);                    \
-    } else {                                                                                \
-      k_slice<kB, B_, S_><<<grid, 256, 0, s>>>(n_lines, K, L, X, op, line_is_col, out, eo,  \
-                                               active);                                     \
-    }                                                                                       \
-    return cudaGetLastError();                                                              \
-  }
-  NEGF_SLICE_CASE(8, 6)
-  NEGF_SLICE_CASE(7, 7)
-  NEGF_SLICE_CASE(6, 8)
-  NEGF_SLICE_CASE(5, 10)
-  NEGF_SLICE_CASE(4, 12)
-  NEGF_SLICE_CASE(3, 12)
-  NEGF_SLICE_CASE(2, 12)
-#undef NEGF_SLICE_CASE
-  return cudaErrorInvalidValue;  // a (beta, S) pair tc_plan never produces
-}
 
 namespace {
 __global__ void k_flag_timeout(const int32_t* err, int P, int32_t* status) {
@@ -1257,20 +907,20 @@ cudaError_t tc_timeout_flag(cudaStream_t s, const TcWs& ws, int P, int32_t* stat
   return cudaGetLastError();
 }
 
-size_t tc_ws_bytes(int P, int M, int N, int K) {
+size_t tc_ws_bytes(int P, int M, int N, int K, int bits) {
   size_t off = 0;
   TcWs w;
-  tc_ws_carve(nullptr, off, P, M, N, K, w);
+  tc_ws_carve(nullptr, off, P, M, N, K, bits, w);
   return off;
 }
 
-void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, TcWs& w) {
+void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, int bits, TcWs& w) {
   // sized for the largest slice count over the K-part policies, so that a configuration
   // change between sizing and use cannot overrun the workspace
   int S = 0;
   for (int mp : {4, 8}) {
     int b2, s2, p2;
-    tc_plan(K, &b2, &s2, &p2, mp);
+    tc_plan(K, bits, &b2, &s2, &p2, mp);
     S = std::max(S, s2);
   }
   const size_t L = (size_t)round_up(2 * K, kKC);
@@ -1289,7 +939,7 @@ void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, TcWs& w) {
 cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<double> A,
                     int opA, BMc<double> B, int opB, z64 beta, BM<double> C, z64 gamma,
                     BMc<double> D, bool add_identity, const int32_t* active, const TcWs& ws,
-                    int n_distinct, bool trunc_a) {
+                    int bits, int n_distinct, bool trunc_a, float* rmax) {
   if (P <= 0 || M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
   // Operands shared by all items (stride 0) or selected per item from n_distinct matrices are
   // sliced once per distinct matrix; the kernel maps each item to its slice set.
@@ -1317,7 +967,7 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
   const int cfg = g_cfg.load();
   const int CG = kShapes[cfg / 2].cg;
   int bta, S, parts;
-  if (!tc_plan(K, &bta, &S, &parts, cfg % 2 == 0 ? 4 : 8))
+  if (!tc_plan(K, bits, &bta, &S, &parts, cfg % 2 == 0 ? 4 : 8))
     return cudaErrorInvalidValue;  // K beyond the exact range (callers check tc_supports_k)
   const int L = round_up(2 * K, kKC);
   const int N2 = 2 * N;
@@ -1339,7 +989,7 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
   if (!make_map(&mB, sb, L, N2, (long long)PB * S, kNT / CG)) return cudaErrorInvalidValue;
 #define NEGF_TC_ARGS                                                                          \
   s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB, zmB, alpha, beta, gamma, C, D, \
-      add_identity, trunc_a ? bta : 0, active
+      add_identity, trunc_a ? bta : 0, active, rmax
   // the windowed schedule does not skip slice orders: truncated products take the plain one
   if (cfg / 2 == kWindowedShape && !trunc_a) return launch_tc<kNT, 6, 1, 1, true>(NEGF_TC_ARGS);
   switch (cfg / 2) {

@@ -15,7 +15,10 @@ import torch
 from . import _build
 
 PREC_FP64 = 0
-PREC_MIXED = 1
+PREC_MIXED = 1       # tensor cores, 48-bit operand values
+PREC_MIXED_40 = 2    # tensor cores, 40-bit operand values
+PREC_MIXED_56 = 3    # tensor cores, 56-bit operand values
+PREC_AUTO = -1       # lead_precision: FP64 for the FP64 form, else 56-bit (48 beyond b = 7008)
 WS_LEAD, WS_RGF, WS_ADJOINT = 0, 1, 2
 
 _STATUS = {
@@ -41,7 +44,8 @@ class _Opt(ctypes.Structure):
     _fields_ = [("eta_lead", c_double), ("eta_device", c_double), ("mu_L", c_double),
                 ("mu_R", c_double), ("kT", c_double), ("sr_tol", c_double),
                 ("sr_max_iter", c_int32), ("precision", c_int32), ("refine_steps", c_int32),
-                ("chunk", c_int32), ("sr_host_check", c_int32), ("adjoint_segment", c_int32)]
+                ("chunk", c_int32), ("sr_host_check", c_int32), ("adjoint_segment", c_int32),
+                ("lead_precision", c_int32), ("refine_max", c_int32)]
 
 
 _LIB = None
@@ -51,7 +55,8 @@ EXPORTS = ("negf_default_options", "negf_abi_version", "negf_status_string",
            "negf_zgemm_batched", "negf_zinv_workspace_size", "negf_zinv_batched",
            "negf_profile_enable", "negf_profile_reset", "negf_profile_read", "negf_profile_flops",
            "negf_launch_count", "negf_zinv_batched_noalloc", "negf_tc_config_count",
-           "negf_tc_config_set", "negf_tc_config_get", "negf_last_cuda_error")
+           "negf_tc_config_set", "negf_tc_config_get", "negf_last_cuda_error",
+           "negf_fp64_fallback_count")
 
 
 def library():
@@ -119,6 +124,8 @@ def library():
     lib.negf_tc_config_get.restype = c_int32
     lib.negf_last_cuda_error.argtypes = []
     lib.negf_last_cuda_error.restype = ctypes.c_char_p
+    lib.negf_fp64_fallback_count.argtypes = []
+    lib.negf_fp64_fallback_count.restype = ctypes.c_longlong
     _LIB = lib
     return lib
 
@@ -387,6 +394,11 @@ def profile_read(kind=PROF_TC_GEMM):
 
 def launch_count() -> int:
     return int(library().negf_launch_count())
+
+
+def fp64_fallback_count() -> int:
+    """Mixed-form block inverses recomputed in FP64 since load (synchronises the device)."""
+    return int(library().negf_fp64_fallback_count())
 
 
 class RGFFunction(torch.autograd.Function):

@@ -37,10 +37,11 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_defaults_and_strings(lib):
-    assert lib.negf_abi_version() == 1
+    assert lib.negf_abi_version() == 2
     o = negf.options()
     assert o.eta_lead == 1e-6 and o.eta_device == 1e-6 and o.sr_max_iter == 100
     assert o.precision == negf.PREC_FP64 and o.refine_steps == 2
+    assert o.lead_precision == negf.PREC_AUTO and o.refine_max == 6
     for code in range(9):
         assert lib.negf_status_string(code)
     assert lib.negf_status_string(99) == b"unknown status"
@@ -108,8 +109,8 @@ def test_binding_refuses_cpu_tensors():
 
 
 def test_options_struct_layout():
-    # six doubles and six 32-bit integers, as in include/negf.h
-    assert ctypes.sizeof(B._Opt) == 6 * 8 + 6 * 4
+    # six doubles and eight 32-bit integers, as in include/negf.h
+    assert ctypes.sizeof(B._Opt) == 6 * 8 + 8 * 4
     assert ctypes.sizeof(B._Dev) == 4 * 4 + 2 * 8
     o = negf.options()
     assert o.sr_host_check == 4
@@ -186,3 +187,31 @@ def test_block_inverse_size_limits_are_checked_on_the_host(lib):
                                    B.WS_RGF) == 0
     assert lib.negf_workspace_size(ctypes.byref(_dev(b=5147)), 1, ctypes.byref(o_fp64),
                                    B.WS_RGF) > 0
+
+
+def test_precision_tiers_and_their_exact_ranges(lib):
+    """Each mixed tier keeps its fixed-point slices exact up to its own contraction length
+    (40 bits: K <= 43648, 48 bits: 28032, 56 bits: 7008) and refuses longer ones on the host; the
+    decimation's automatic precision is the 56-bit tier where it is exact, else the 48-bit one."""
+    for prec, kmax in ((B.PREC_MIXED_40, 43648), (B.PREC_MIXED, 28032), (B.PREC_MIXED_56, 7008)):
+        assert lib.negf_zgemm_workspace_size(prec, 1, 8, 8, kmax) > 0
+        assert lib.negf_zgemm_workspace_size(prec, 1, 8, 8, kmax + 1) == 0
+    # 56-bit values need more slices: a larger workspace for the same product
+    w48 = lib.negf_zgemm_workspace_size(B.PREC_MIXED, 4, 400, 400, 400)
+    w56 = lib.negf_zgemm_workspace_size(B.PREC_MIXED_56, 4, 400, 400, 400)
+    w40 = lib.negf_zgemm_workspace_size(B.PREC_MIXED_40, 4, 400, 400, 400)
+    assert w40 < w48 < w56
+    assert lib.negf_zgemm_workspace_size(4, 1, 8, 8, 8) == 0
+    d = _dev(b=400)
+    auto = negf.options(precision=B.PREC_MIXED)
+    l48 = negf.options(precision=B.PREC_MIXED, lead_precision=B.PREC_MIXED)
+    l56 = negf.options(precision=B.PREC_MIXED, lead_precision=B.PREC_MIXED_56)
+    size = lambda o, dv=d: lib.negf_workspace_size(ctypes.byref(dv), 8, ctypes.byref(o), B.WS_LEAD)
+    assert size(auto) == size(l56) > size(l48) > 0
+    # beyond b = 7008 the automatic lead precision falls back to 48 bits
+    big = _dev(b=8000)
+    assert size(auto, big) == size(l48, big) > 0 and size(l56, big) == 0
+    for bad in (dict(lead_precision=5), dict(lead_precision=-2), dict(refine_max=17),
+                dict(refine_max=-1)):
+        o = negf.options(precision=B.PREC_MIXED, **bad)
+        assert lib.negf_workspace_size(ctypes.byref(d), 8, ctypes.byref(o), B.WS_LEAD) == 0

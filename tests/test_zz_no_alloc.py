@@ -51,6 +51,28 @@ def test_noalloc_inverse_matches_workspace_inverse(n):
         assert np.allclose(X @ M, np.eye(n), atol=1e-9)
 
 
+def test_noalloc_small_blocks_need_no_scratch():
+    """Blocks of n <= 106 are eliminated in shared memory, so any batch size is accepted: a
+    batch whose panel scratch would exceed the fixed array still runs and matches."""
+    negf._build.build()
+    lib = negf.library()
+    n, nb = 48, 2000
+    M = _problem(21, nb, n)
+    ref, _ = negf.zinv(torch.as_tensor(M.copy(), device="cuda"), precision=negf.PREC_FP64)
+    Md = torch.as_tensor(M.copy(), device="cuda")
+    X = torch.empty_like(Md)
+    st = torch.full((nb,), -1, dtype=torch.int32, device="cuda")
+    rc = lib.negf_zinv_batched_noalloc(nb, n, ctypes.c_void_p(Md.data_ptr()),
+                                       ctypes.c_void_p(X.data_ptr()),
+                                       ctypes.c_void_p(st.data_ptr()),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert np.all(st.cpu().numpy() == 0)
+    X, ref = X.cpu().numpy(), ref.cpu().numpy()
+    assert np.abs(X - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
 def test_noalloc_rejects_oversize_batch():
     negf._build.build()
     lib = negf.library()
