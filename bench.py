@@ -31,12 +31,12 @@ WORK = dict(N=70, b=400, n_E=512, n_k=8, ge_frac=0.1, eta=1e-6, seed=1001,
             name="ballistic RGF, N=70 slabs x 400x400 blocks, alloy p(Ge)=0.1, 512 E x 8 k")
 METRIC = "RGF energy-points/s (leads + forward/backward sweeps + observables + FP64 quadrature)"
 PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0)
-# DRAM bytes (read + write) of k_tc_gemm per 400 x 400 x 400 complex item, from the ncu capture
-# summarised in profiles/tc_gemm_b400_x64.md (64 items: 930.8 MB read + 155.7 MB written) of
-# tensor-core configuration TC_PROFILED_CONFIG; reported only when the bench runs that
-# configuration.  The traffic of a launch scales with its items.
-TC_DRAM_BYTES_PER_ITEM_B400 = (930.753024e6 + 155.679488e6) / 64
+# DRAM bytes (read + write) of k_tc_gemm per 400 x 400 x 400 complex item from an ncu capture of
+# a 64-item launch of tensor-core configuration TC_PROFILED_CONFIG, scaled by the items of a
+# launch; None while the kernel has changed since the capture (the line then reports null).
+TC_DRAM_BYTES_PER_ITEM_B400 = None
 TC_PROFILED_CONFIG = 20
+GOLDEN = os.path.join(ROOT, "tests", "golden", "c1_oracle.json")
 
 
 def parse():
@@ -48,7 +48,12 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--points-per-step", type=int, default=256)
     ap.add_argument("--cpu-points", type=int, default=4)
-    ap.add_argument("--fp64-points", type=int, default=4)
+    ap.add_argument("--fp64-points", type=int, default=64,
+                    help="points of the FP64 GPU comparison batch (one batch; the FP64 form's "
+                         "rate saturates near 64 points on this device)")
+    ap.add_argument("--no-golden", action="store_true",
+                    help="skip the accuracy check of a full k-slice against the stored oracle "
+                         "values (tests/golden/c1_oracle.json)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU-oracle, FP64-GPU and end-to-end side measurements")
     ap.add_argument("--workload", default="rgf",
@@ -414,6 +419,14 @@ def main():
     launches = negf.launch_count() - l0
     negf.profile(False)
     ms = max_over_ranks(ev0.elapsed_time(ev1), dist, dvc)
+    # one more step without the per-launch profiling events (instrumentation overhead check)
+    torch.cuda.synchronize()
+    ev2, ev3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev2.record()
+    step(args.warmup)
+    ev3.record()
+    torch.cuda.synchronize()
+    ms_noprof = ev2.elapsed_time(ev3)
     n_launch, tc_ms, alg, hw = negf.profile_read(negf.PROF_TC_GEMM)
     sl_n, sl_ms, _, _ = negf.profile_read(negf.PROF_SLICE)
     inv_n, inv_ms, _, _ = negf.profile_read(negf.PROF_INV)
@@ -441,7 +454,8 @@ def main():
                     if TC_DRAM_BYTES_PER_ITEM_B400 and WORK["b"] == 400 and n_launch
                     and prec == negf.PREC_MIXED and negf.tc_config() == TC_PROFILED_CONFIG
                     else None),
-        "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
+        "traffic_unit": "bytes per launch (DRAM read + write, ncu capture of 64 items scaled "
+                        "to the launch's items)",
     }
     line = {
         "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
@@ -453,11 +467,15 @@ def main():
                    "l2": "inputs > L2: each step streams 358 MB of H blocks",
                    "parallelism": f"points sharded over {world} rank(s), no data-path collective", "tc_config": tuned},
         "gpu_launches": int(launches), "clocks": clk.summary(), "roofline": roofline,
+        "ms_per_step_profiling_off": ms_noprof,
     }
     if rank == 0 and not args.no_extras:
         line.update(extras(args, negf, torch, device, dvc, Hd, dev_np, E, wE, wk, prec))
         if "fp64_gpu" in line:
             line["speedup_vs_fp64_gpu"] = value / world / line["fp64_gpu"]["value"]
+        if not args.no_golden and os.path.exists(GOLDEN):
+            line["rel_err_vs_oracle_kslice"] = golden_check(negf, torch, device, dvc, E, wE,
+                                                            prec, P)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -545,8 +563,71 @@ def extras(args, negf, torch, device, dvc, Hd, dev_np, E, wE, wk, prec):
         torch.cuda.synchronize()
         v64 = fpn / (ev0.elapsed_time(ev1) / 1e3)
         out["fp64_gpu"] = {"value": v64, "unit": "points/s", "points": fpn,
-                           "sample": f"{fpn} points of the workload in one batch"}
+                           "sample": f"{fpn} points of the workload in one batch (the FP64 "
+                                     "form's rate saturates with the batch: 0.93 / 1.35 / 1.59 "
+                                     "points/s at 4 / 16 / 64 points)"}
     return out
+
+
+def golden_check(negf, torch, device, dvc, E, wE, prec, P):
+    """Accuracy of this run's options against stored oracle values of the same device: every
+    energy of one k-slice (energy integrals of the per-atom density and of the bond currents,
+    T(E)) and per-point values at 64 stored points (48 on that slice, 16 on the -k slice)."""
+    with open(GOLDEN) as fh:
+        gd = json.load(fh)
+    N, b = WORK["N"], WORK["b"]
+    km, kp = gd["k_main"], gd["k_partner"]
+    opt = negf.options(precision=prec, chunk=P)
+    n_E = len(E)
+    dens_int = torch.zeros((1, N * b), dtype=torch.float64, device=dvc)
+    cur_int = torch.zeros((1, N - 1), dtype=torch.float64, device=dvc)
+    T = np.empty(n_E)
+    per = {}
+    want = {(q["k_index"], q["energy_index"]) for q in gd["points"]}
+    jobs = [(km, np.arange(s, min(s + P, n_E))) for s in range(0, n_E, P)]
+    part = sorted(e for (k, e) in want if k == kp)
+    if part:
+        jobs.append((kp, np.array(part)))
+    for k, idx in jobs:
+        Et = torch.as_tensor(E[idx], device=dvc)
+        st = torch.full((len(idx),), k, dtype=torch.int32, device=dvc)
+        lead = negf.lead_selfenergy(device, Et, st, opt)
+        r = negf.rgf_solve(device, Et, st, lead["sigma_R"], lead["sigma_L"], opt)
+        if k == km:
+            w = torch.as_tensor(wE[idx], device=dvc)
+            dens_int += negf.integrate(r["density"], w)
+            cur_int += negf.integrate(r["current"], w)
+            T[idx] = r["transmission"].cpu().numpy()
+        dn = r["density"].reshape(len(idx), N, b).sum(dim=2).cpu().numpy()
+        cu = r["current"].cpu().numpy()
+        tr = r["transmission"].cpu().numpy()
+        for q, e in enumerate(idx):
+            if (k, int(e)) in want:
+                per[(k, int(e))] = (dn[q], cu[q], tr[q])
+    atoms = dens_int.reshape(-1, 10).sum(dim=1).cpu().numpy()
+    jint = cur_int.reshape(-1).cpu().numpy()
+
+    def rel(a, ref):
+        return float(np.abs(np.asarray(a) - np.asarray(ref)).max() / np.abs(ref).max())
+    jscale = max(np.abs(q["current"]).max() for q in gd["points"] if q["k_index"] == km)
+    pd, pj, pt = [], [], []
+    for q in gd["points"]:
+        dn, cu, tr = per[(q["k_index"], q["energy_index"])]
+        pd.append(rel(dn, q["slab_density"]))
+        pj.append(float(np.abs(cu - np.asarray(q["current"])).max() / jscale))
+        pt.append(abs(tr - q["transmission"]) / max(1.0, abs(q["transmission"])))
+    Tref = np.asarray(gd["transmission_main"])
+    return {
+        "integrated_density_per_atom": rel(atoms, gd["integrated_atom_density_main"]),
+        "integrated_current": rel(jint, gd["integrated_current_main"]),
+        "transmission_max": float(np.abs(T - Tref).max() / max(1.0, np.abs(Tref).max())),
+        "points": len(pd), "slab_density_per_point_max": max(pd),
+        "current_per_point_max": max(pj), "transmission_per_point_max": max(pt),
+        "norm": ("inf-norm relative; per-point current relative to the largest stored current "
+                 "of the slice (outside the bias window j(E) ~ (f_L - f_R) T vanishes)"),
+        "sample": f"k-slice {km} (512 energies, trapezoid weights) + {len(part)} points of slice "
+                  f"{kp}, stored oracle values",
+    }
 
 
 if __name__ == "__main__":

@@ -73,10 +73,11 @@ typedef enum {
 
 /* Precision forms.  The mixed forms run every block GEMM on the tensor cores: each row of
  * op(A) and column of op(B) is scaled by a power of two and rounded once to a fixed-point value
- * of 40, 48 or 56 bits, cut into exact BF16 slices whose products are summed exactly in FP32
- * groups; storage, pivoting, norms and reductions stay FP64.  A product's error is about
+ * of 39, 47 or 55 bits below twice the line maximum (the tiers are named 40, 48 and 56 bits),
+ * cut into exact BF16 slices whose products are summed exactly in FP32 groups; storage,
+ * pivoting, norms and reductions stay FP64.  A product's error is about
  * 2^-bits x K x max|row of A| x max|column of B|.  Issued tensor work per complex product: 15
- * (40 bits), 28 (48 bits) or 36 (56 bits) slice products for 400 x 400 blocks. */
+ * (40 bits), 21 (48 bits) or 28 (56 bits) slice products for blocks up to 512 x 512. */
 typedef enum {
   NEGF_PREC_FP64 = 0,     /* every block operation in FP64 on the CUDA cores (reference form) */
   NEGF_PREC_MIXED = 1,    /* tensor cores, 48-bit operand values (the default mixed form)     */
@@ -84,7 +85,7 @@ typedef enum {
   NEGF_PREC_MIXED_56 = 3  /* tensor cores, 56-bit operand values (FP64-class products)        */
 } negf_precision;
 /* negf_options.lead_precision: FP64 when `precision` is FP64, else NEGF_PREC_MIXED_56 (or
- * NEGF_PREC_MIXED for blocks beyond its exact range, b > 7008).  The
+ * NEGF_PREC_MIXED for blocks beyond its exact range).  The
  * decimation of a lead whose finite segments have near-singular (z - eps) blocks amplifies the
  * rounding of its early steps by up to ~1e9 (measured on the benchmark device); 56-bit products
  * keep its error at the level of an FP64 decimation. */
@@ -250,8 +251,8 @@ negf_status negf_integrate(int32_t n_pts, int32_t len, int32_t n_groups, const d
  * between batch items (0 = the same matrix for every item; C needs a nonzero stride when
  * n_batch > 1).  `precision` is any negf_precision.  FP64 form: CUDA cores.  Mixed forms:
  * tensor cores with exact split-BF16 slices of 40-, 48- or 56-bit values (error about
- * 2^-bits x K relative to max|A| max|B| per row and column), exact for K <= 43648
- * (40 bits), 28032 (48 bits) or 7008 (56 bits): a longer contraction returns
+ * 2^-bits x K relative to max|A| max|B| per row and column), exact for K <= 524288
+ * (40 bits), 393216 (48 bits) or 98304 (56 bits): a longer contraction returns
  * NEGF_ERR_UNSUPPORTED (and a workspace size of 0) rather than losing accuracy.  The block
  * inverse (and so every sweep entry point) takes
  * blocks up to n = 5147 in FP64 and n = 9266 in the mixed form (its Gauss-Jordan panel lives
@@ -303,15 +304,15 @@ negf_status negf_zinv_batched_noalloc(int32_t n_batch, int32_t n, double* M, dou
  * The mixed-precision GEMM has negf_tc_config_count() kernel configurations, differing only in
  * speed: configuration c uses the kernel shape c / 2 of
  *   (6 stages, 1 CTA, 1), (6, 1, 2), (6, 1, 3), (8 stages, CTA pair, 1), (8, 2, 2), (8, 2, 4),
- *   (6, 1, 1, windowed), (3, 1, 1, 2 K chunks per stage), (4, 2, 1, 2 K chunks per stage),
+ *   (3, 1, 1, 2 K chunks per stage), (4, 2, 1, 2 K chunks per stage),
  *   (2, 1, 1, 3 K chunks per stage), (2, 2, 1, 4 K chunks per stage)
  * = (shared-memory pipeline stages, CTAs per MMA: one 128-row tile or a pair of CTAs with a
- * 256-row MMA, stages released per MMA commit; windowed: slice orders taken two at a time so
- * that each loaded B slice tile serves two products; K chunks of 64 per stage) and splits K
- * into at most (4, 8)[c % 2] exactly accumulated parts (more parts allow wider slices and fewer
- * slice products).
- * negf_tc_config_set selects one process-wide (default 18); results agree to the GEMM's
- * rounding.  The package's autotuner times them per block size and stores the choice. */
+ * 256-row MMA, stages released per MMA commit; K chunks of 64 per stage) and splits K into at
+ * most (4, 8)[c % 2] exactly accumulated parts (more parts allow wider slices and fewer slice
+ * products for long contractions).
+ * negf_tc_config_set selects one process-wide (default 18: the CTA pair with 2 stages of 4 K
+ * chunks); results agree to the GEMM's rounding.  The package's autotuner times them per block
+ * size and stores the choice. */
 int32_t negf_tc_config_count(void);
 negf_status negf_tc_config_set(int32_t idx);
 int32_t negf_tc_config_get(void);
@@ -329,10 +330,19 @@ int32_t negf_tc_config_get(void);
 void negf_profile_enable(int32_t on);
 void negf_profile_reset(void);
 negf_status negf_profile_read(int32_t kind, long long* launches, double* total_ms);
-/* Flops dispatched to kind 0 since the last reset: complex algorithmic 8 M N K per batch item,
- * and the BF16 tensor-core flops actually issued (all slice products over the padded tiles). */
+/* Flops of kind 0 since the last reset, counted on the device for the batch items that ran
+ * (items masked off, e.g. blocks whose Newton-Schulz refinement had converged, do not count):
+ * complex algorithmic 8 M N K per item, and the BF16 tensor-core flops actually issued (the
+ * computed slice products over the padded tiles).  Reading and resetting synchronise the
+ * current device. */
 negf_status negf_profile_flops(int32_t kind, double* algorithmic, double* hardware);
 long long negf_launch_count(void);
+/* Test hook for the timeout reporting path: while `on` is nonzero, every mixed-form call ends
+ * as if a bounded wait inside one of its tensor-core GEMMs had given up (the device error word
+ * is set on the call's stream before the per-point status is written), so NEGF_PT_TIMEOUT is
+ * set for every point without any GPU wait having to expire.  The outputs are not touched.
+ * Process-wide; off by default; for tests only. */
+void negf_debug_fail_waits(int32_t on);
 /* Name of the last CUDA runtime error that made a call of this library return NEGF_ERR_CUDA
  * (e.g. "cudaErrorInvalidValue"; "cudaSuccess" if none), for diagnostics.  Static string. */
 const char* negf_last_cuda_error(void);

@@ -1,4 +1,6 @@
 // Engine dispatch: FP64 reference form and the mixed-precision tensor-core form.
+#include <atomic>
+
 #include "engine.cuh"
 #include "profile.cuh"
 #include "tc_gemm.cuh"
@@ -123,10 +125,21 @@ cudaError_t Engine::timeout_reset() {
   return tc_timeout_reset(s, tc_view(w, 1, b, prec_bits(prec)));
 }
 
+namespace {
+std::atomic<int> g_fail_waits{0};
+}
+
 cudaError_t Engine::timeout_flag(int P, int32_t* status) {
   if (!prec_mixed(prec)) return cudaSuccess;
-  return tc_timeout_flag(s, tc_view(w, 1, b, prec_bits(prec)), P, status);
+  const TcWs tw = tc_view(w, 1, b, prec_bits(prec));
+  if (g_fail_waits.load()) {  // test hook: report as if a bounded wait had given up
+    cudaError_t e = cudaMemsetAsync(tw.err, 1, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+  }
+  return tc_timeout_flag(s, tw, P, status);
 }
+
+void engine_fail_waits(int on) { g_fail_waits.store(on ? 1 : 0); }
 
 cudaError_t Engine::inv(int P, BM<double> Mm, BM<double> X, int32_t* status,
                         const int32_t* active) {

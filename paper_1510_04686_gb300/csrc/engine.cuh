@@ -77,6 +77,8 @@ struct Engine {
 // Number of block inverses (on the current device) that the mixed form recomputed in FP64
 // because Newton-Schulz did not reach its residual target (synchronises the device).
 long long engine_fp64_fallbacks();
+// Test hook: with `on`, every mixed-form timeout check reports a given-up wait.
+void engine_fail_waits(int on);
 
 // Whether this build implements the precision form (negf_precision) for blocks of size b: the
 // block inverse launches up to b = 5147 (FP64) / 9266 (mixed, FP32 elimination), and the mixed

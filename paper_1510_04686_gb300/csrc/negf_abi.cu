@@ -407,6 +407,8 @@ int32_t negf_abi_version(void) { return NEGF_ABI_VERSION; }
 
 long long negf_fp64_fallback_count(void) { return engine_fp64_fallbacks(); }
 
+void negf_debug_fail_waits(int32_t on) { engine_fail_waits(on); }
+
 const char* negf_status_string(negf_status s) {
   switch (s) {
     case NEGF_OK: return "ok";

@@ -5,6 +5,7 @@
 
 #include "common.cuh"
 #include "profile.cuh"
+#include "tc_gemm.cuh"
 
 namespace negf {
 namespace {
@@ -104,6 +105,7 @@ negf_status negf_profile_read(int32_t kind, long long* launches, double* total_m
 
 void negf_profile_reset(void) {
   std::lock_guard<std::mutex> lk(g_mu);
+  tc_prof_reset();
   for (int k = 0; k < PROF_KINDS; ++k) {
     g_count[k] = 0;
     g_ms[k] = 0.0;
@@ -115,6 +117,10 @@ void negf_profile_reset(void) {
 negf_status negf_profile_flops(int32_t kind, double* algorithmic, double* hardware) {
   if (kind < 0 || kind >= PROF_KINDS || !algorithmic || !hardware) return NEGF_ERR_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
+  if (kind == PROF_TC_GEMM) {  // counted on the device, for the batch items that ran
+    if (tc_prof_flops(algorithmic, hardware) != cudaSuccess) return NEGF_ERR_CUDA;
+    return NEGF_OK;
+  }
   *algorithmic = g_alg[kind];
   *hardware = g_hw[kind];
   return NEGF_OK;

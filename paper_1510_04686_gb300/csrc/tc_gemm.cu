@@ -29,20 +29,15 @@ constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on every dev
 
 constexpr int kMaxParts = 8;
 struct Item {
-  int8_t acc, s, t, kp;  // accumulator group, A slice, B slice, K part
+  uint8_t acc;          // exact accumulator group
+  int8_t s, t, kp;      // A slice, B slice (1-based), K part
 };
-constexpr int kMaxWin = 16;
 struct Sched {
   int n_items;
   int n_acc;
   int part_lo[kMaxParts];  // first K chunk of each part
   int part_hi[kMaxParts];  // one past the last K chunk
-  Item it[kMaxItems];
-  // windowed schedule: per part, windows of one order d or of two orders (d, d + 1)
-  int n_parts;
-  int n_win;
-  int8_t win_d[kMaxWin];
-  int8_t win_pair[kMaxWin];
+  Item it[kMaxItems];      // grouped: the items of one accumulator group are consecutive
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -176,6 +171,10 @@ __device__ __forceinline__ double f32_scaled(uint32_t xb, int k) {
 }
 
 
+// Flops of the launches made while profiling is on: [0] algorithmic complex 8 M N K of the
+// active items, [1] issued BF16 MMA flops (padded tiles, computed slice products).
+__device__ double g_tc_prof[2];
+
 __device__ __forceinline__ float warp_max_f(float v) {
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
@@ -248,17 +247,9 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
                : "memory");
 }
 
-// WIN: windowed schedule (CG = 1, G = 1).  The slice orders of a part are taken in windows of
-// one order {d} or two orders {d, d + 1}; a window walks its A slices s = 1, 2, ... and each
-// shared-memory stage holds (A_s, B_{d+1-s}).  A step issues A_s x B_{d+1-s} into order d and
-// A_s x B_{d+2-s} (the previous stage's B tile, still resident) into order d + 1, so one B tile
-// serves two products: for S = 7 a K chunk moves 32 tiles instead of 56 for the same 28
-// products.  A stage whose B tile the next step reuses is released one step later; the two
-// accumulators of a pair window are both live, so the MMAs wait for the epilogue between
-// windows.
 // KPS: K chunks (of 64 BF16 columns) per shared-memory stage; more chunks per stage put more
 // MMAs behind each barrier wait and commit of the MMA thread.
-template <int NT, int STAGES, int CG, int G, bool WIN, int KPS = 1>
+template <int NT, int STAGES, int CG, int G, int KPS = 1>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const Sched sched, int M, int N2, int S, int two_beta,
@@ -266,12 +257,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int32_t* __restrict__ zidxA, int zmodeA, const int32_t* __restrict__ zidxB,
               int zmodeB, z64 alpha,
               z64 beta, z64 gamma, BM<double> C, BMc<double> D, int add_identity,
-              int trunc_beta, const int32_t* active, int32_t* err, float* rmax) {
+              int trunc_beta, const int32_t* active, int32_t* err, float* rmax, int Kc,
+              int count_flops) {
   static_assert(NT * (kAccBufs + 2) == 512, "TMEM: kAccBufs accumulators + hi / lo sum words");
   static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair per MMA");
-  static_assert(!WIN || (CG == 1 && G == 1), "windowed schedule: one CTA, one stage per commit");
   using CF = Cfg<NT, STAGES, CG, G, KPS>;
-  static_assert(!WIN || KPS == 1, "windowed schedule: one K chunk per stage");
   constexpr int kStages = CF::kStages;
   const int p = blockIdx.z;
   // both CTAs of a pair have the same item, so they leave together (before any cluster barrier)
@@ -287,6 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accempty + kAccBufs);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* s_cut = reinterpret_cast<int*>(tmem_slot + 2);
+  int* s_nexec = reinterpret_cast<int*>(tmem_slot + 3);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * NT;  // pairs are adjacent along x
@@ -317,6 +308,29 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (fmax < 0) cut = max(1, S - (-fmax) / trunc_beta);
     }
     *s_cut = cut;
+    // accumulator groups this tile computes (a group holds products of one order)
+    int nex = 0, prev = -1;
+    for (int ii = 0; ii < sched.n_items; ++ii) {
+      const Item it = sched.it[ii];
+      if (it.s + it.t - 1 <= cut && (int)it.acc != prev) {
+        ++nex;
+        prev = it.acc;
+      }
+    }
+    *s_nexec = nex;
+    if (count_flops) {
+      // this CTA's share of the launch (its own 128 rows; in a pair the even CTA's MMAs cover
+      // both CTAs' rows): algorithmic complex flops of its outputs and issued BF16 MMA flops
+      const int rows = max(0, min(kBM, M - m0));
+      const int cols = max(0, min(NT / 2, (N2 >> 1) - n0 / 2));
+      double chunks = 0.0;
+      for (int ii = 0; ii < sched.n_items; ++ii) {
+        const Item it = sched.it[ii];
+        if (it.s + it.t - 1 <= cut) chunks += sched.part_hi[it.kp] - sched.part_lo[it.kp];
+      }
+      atomicAdd(&g_tc_prof[0], 8.0 * rows * cols * (double)Kc);
+      atomicAdd(&g_tc_prof[1], 2.0 * kBM * NT * kKC * chunks);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 9) {
@@ -338,126 +352,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const int cut = *s_cut;
+  const int n_exec = *s_nexec;
 
-  if (WIN && warp == 8) {
-    // ---------------- TMA producer, windowed schedule
-    if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      bool ok = true;
-      for (int q = 0; q < sched.n_parts && ok; ++q)
-        for (int w = 0; w < sched.n_win && ok; ++w) {
-          const int d = sched.win_d[w];
-          const bool pair = sched.win_pair[w] != 0;
-          const int nsteps = pair ? d + 2 : d;
-          for (int kc = sched.part_lo[q]; kc < sched.part_hi[q] && ok; ++kc)
-            for (int st = 0; st < nsteps; ++st) {
-              // pair: step 0 loads B_{d+1}; step s loads (A_s, B_{d+1-s}); step d+1 loads A_{d+1}
-              // single order: step st loads (A_{st+1}, B_{d-st})
-              const int a = pair ? st : st + 1;
-              const int bs = pair ? (st <= d ? d + 1 - st : 0) : d - st;
-              if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) {
-                ok = false;
-                break;
-              }
-              unsigned char* stp = smem + stage * CF::kStage;
-              mbar_expect_tx(&full[stage], (a ? CF::kATile : 0) + (bs ? CF::kBTile : 0));
-              if (a) tma_load_3d(stp, &mapA, &full[stage], kc * kKC, m0, zA * S + a - 1);
-              if (bs)
-                tma_load_3d(stp + CF::kATile, &mapB, &full[stage], kc * kKC, n0, zB * S + bs - 1);
-              if (++stage == kStages) {
-                stage = 0;
-                phase ^= 1;
-              }
-            }
-        }
-      for (int i = 0; i < kStages; ++i) {  // drain: every stage is released by the MMAs
-        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
-        if (++stage == kStages) {
-          stage = 0;
-          phase ^= 1;
-        }
-      }
-    }
-  } else if (WIN && warp == 9) {
-    // ---------------- MMA issuer, windowed schedule
-    if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kBM, NT);
-      int stage = 0;
-      uint32_t phase = 0;
-      int held = -1;  // stage whose B tile the current step still reads
-      uint32_t acc_on[2] = {0, 0};
-      bool ok = true;
-      auto start_group = [&](int g) -> bool {
-        if (g >= 2) {
-          if (!mbar_wait(&accempty[g & 1], ((g >> 1) - 1) & 1, abort_flag)) return false;
-          tc_fence_after();
-        }
-        acc_on[g & 1] = 0;
-        return true;
-      };
-      auto product = [&](int g, uint32_t a_addr, uint32_t b_addr) {
-        const uint32_t dcol = tmem + (uint32_t)((g & 1) * NT);
-#pragma unroll
-        for (int k = 0; k < kKC / 16; ++k) {
-          mma_bf16(dcol, sw128_desc(a_addr + 32 * k), sw128_desc(b_addr + 32 * k), idesc,
-                   acc_on[g & 1]);
-          acc_on[g & 1] = 1;
-        }
-      };
-      for (int q = 0; q < sched.n_parts && ok; ++q)
-        for (int w = 0; w < sched.n_win && ok; ++w) {
-          const int d = sched.win_d[w];
-          const bool pair = sched.win_pair[w] != 0;
-          const int nsteps = pair ? d + 2 : d;
-          const int gA = q * S + d - 1;  // group of order d (order d + 1: gA + 1)
-          for (int kc = sched.part_lo[q]; kc < sched.part_hi[q] && ok; ++kc) {
-            const bool first = (kc == sched.part_lo[q]), lastk = (kc == sched.part_hi[q] - 1);
-            for (int st = 0; st < nsteps; ++st) {
-              if (!mbar_wait(&full[stage], phase, abort_flag)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              const uint32_t a0 = smem_u32(smem + stage * CF::kStage);
-              if (pair) {
-                if (st >= 1 && st <= d) {  // A_s x B_{d+1-s} (this stage) into order d
-                  if (first && st == 1 && !(ok = start_group(gA))) break;
-                  product(gA, a0, a0 + CF::kATile);
-                }
-                if (st >= 1) {  // A_s x B_{d+2-s} (previous stage) into order d + 1
-                  if (first && st == 1 && !(ok = start_group(gA + 1))) break;
-                  product(gA + 1, a0, smem_u32(smem + held * CF::kStage) + CF::kATile);
-                }
-              } else {
-                if (first && st == 0 && !(ok = start_group(gA))) break;
-                product(gA, a0, a0 + CF::kATile);
-              }
-              if (held >= 0) {  // the previous stage's B tile has served its second product
-                mma_commit(&empty[held]);
-                held = -1;
-              }
-              if (pair && st <= d)
-                held = stage;  // the next step reads this stage's B tile
-              else
-                mma_commit(&empty[stage]);
-              if (lastk) {
-                if (pair) {
-                  if (st == d) mma_commit(&accfull[gA & 1]);
-                  if (st == d + 1) mma_commit(&accfull[(gA + 1) & 1]);
-                } else if (st == d - 1) {
-                  mma_commit(&accfull[gA & 1]);
-                }
-              }
-              if (++stage == kStages) {
-                stage = 0;
-                phase ^= 1;
-              }
-            }
-          }
-        }
-    }
-  } else if (warp == 8) {
+  if (warp == 8) {
     // ---------------- TMA producer: for every item, the K chunks of its part
     if (lane == 0) {
       int stage = 0;
@@ -611,7 +508,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int cbase = half * (NT / 2);
     const uint32_t t_hi = tmem + lane_off + kAccBufs * NT, t_lo = t_hi + NT;
-    const int n_exec = (sched.n_acc / S) * min(cut, S);  // groups of orders <= cut per part
     float omax = 0.0f;  // largest |Re|, |Im| this thread stores (for rmax)
     for (int acc = 0; acc < n_exec; ++acc) {
       const int buf = acc % kAccBufs;
@@ -754,40 +650,31 @@ bool make_map(CUtensorMap* m, void* base, int L, int rows, long long zdim, int b
 
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-// Exact accumulator groups: for every K part and every order d = s + t - 1 <= S, one group
-// holding the products (s, t) of that order over that part of K.
-Sched build_sched(int S, int n_chunks, int n_parts) {
+// Exact accumulator groups: for every K part and every order d = s + t - 1 <= S, the products
+// (s, t) of that order over that part, gsize products per group.
+Sched build_sched(const TcPlan& pl, int n_chunks) {
   Sched sc;
   std::memset(&sc, 0, sizeof(sc));
-  n_parts = std::max(1, std::min(n_parts, std::min(kMaxParts, n_chunks)));
+  const int n_parts = std::max(1, std::min(pl.parts, std::min(kMaxParts, n_chunks)));
   for (int q = 0; q < n_parts; ++q) {
     sc.part_lo[q] = (int)((long long)n_chunks * q / n_parts);
     sc.part_hi[q] = (int)((long long)n_chunks * (q + 1) / n_parts);
   }
   int n = 0, g = 0;
   for (int q = 0; q < n_parts; ++q)
-    for (int d = 1; d <= S; ++d, ++g)
-      for (int s = 1; s <= d && n < kMaxItems; ++s)
-        sc.it[n++] = Item{(int8_t)g, (int8_t)s, (int8_t)(d + 1 - s), (int8_t)q};
+    for (int d = 1; d <= pl.S; ++d, ++g)
+      for (int s = 1; s <= d && n < kMaxItems; ++s) {
+        if (s > 1 && (s - 1) % pl.gsize == 0) ++g;
+        sc.it[n++] = Item{(uint8_t)g, (int8_t)s, (int8_t)(d + 1 - s), (int8_t)q};
+      }
   sc.n_items = n;
   sc.n_acc = g;
-  sc.n_parts = n_parts;
-  // windows {1}, {2, 3}, {4, 5}, ... (a last single order when S is even)
-  int w = 0;
-  sc.win_d[w] = 1;
-  sc.win_pair[w++] = 0;
-  for (int d = 2; d <= S && w < kMaxWin; d += 2) {
-    sc.win_d[w] = (int8_t)d;
-    sc.win_pair[w++] = (int8_t)(d + 1 <= S ? 1 : 0);
-  }
-  sc.n_win = w;
   return sc;
 }
 
-
-template <int NT, int STAGES, int CG, int G, bool WIN = false, int KPS = 1>
-cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S, int two_beta,
-                      int n_parts, const CUtensorMap& mA, const CUtensorMap& mB, const TcWs& ws,
+template <int NT, int STAGES, int CG, int G, int KPS = 1>
+cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int S, int two_beta,
+                      const Sched& sc, const CUtensorMap& mA, const CUtensorMap& mB, const TcWs& ws,
                       const int32_t* zA, int zmA, const int32_t* zB, int zmB, z64 alpha,
                       z64 beta, z64 gamma, BM<double> C, BMc<double> D, bool add_identity,
                       int trunc_beta, const int32_t* active, float* rmax) {
@@ -795,21 +682,14 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
   static std::atomic<unsigned> attr{0};
   {
     cudaError_t e = set_smem_once(
-        attr, reinterpret_cast<const void*>(&k_tc_gemm<NT, STAGES, CG, G, WIN, KPS>), CF::kSmem);
+        attr, reinterpret_cast<const void*>(&k_tc_gemm<NT, STAGES, CG, G, KPS>), CF::kSmem);
     if (e != cudaSuccess) return e;
   }
-  if ((long long)std::min(n_parts, kMaxParts) * S * (S + 1) / 2 > kMaxItems)
-    return cudaErrorInvalidValue;  // schedule longer than the kernel's item table
-  Sched sc = build_sched(S, L / kKC, n_parts);
   const int mt = (M + kBM - 1) / kBM;
   // x: row tiles (a CTA pair is two x-adjacent CTAs, so the count is even for pairs), y: columns
   dim3 grid((mt + CG - 1) / CG * CG, (N2 + NT - 1) / NT, P);
   if (grid.y > 65535) return cudaErrorInvalidValue;
-  {
-    const double alg = 8.0 * M * (N2 / 2) * (double)K * P;
-    const double hw = 2.0 * grid.x * kBM * (double)grid.y * NT * L * (S * (S + 1) / 2) * P;
-    prof_flops(PROF_TC_GEMM, alg, hw);
-  }
+  const int count_flops = profiling_on() ? 1 : 0;
   prof_begin(s, PROF_TC_GEMM);
   cudaLaunchConfig_t lc = {};
   lc.gridDim = grid;
@@ -823,10 +703,11 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int L, int S,
   at[0].val.clusterDim.z = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&lc, k_tc_gemm<NT, STAGES, CG, G, WIN, KPS>, mA, mB, sc, M, N2, S,
+  cudaError_t e = cudaLaunchKernelEx(&lc, k_tc_gemm<NT, STAGES, CG, G, KPS>, mA, mB, sc, M, N2, S,
                                      two_beta, (const int32_t*)ws.expA, (const int32_t*)ws.expB,
                                      zA, zmA, zB, zmB, alpha, beta, gamma, C, D,
-                                     add_identity ? 1 : 0, trunc_beta, active, ws.err, rmax);
+                                     add_identity ? 1 : 0, trunc_beta, active, ws.err, rmax,
+                                     K, count_flops);
   prof_end(s, PROF_TC_GEMM);
   count_launch();
   if (e != cudaSuccess) return e;
@@ -843,49 +724,59 @@ struct TcShape {
   int stages, cg, grp;
 };
 constexpr TcShape kShapes[] = {{6, 1, 1}, {6, 1, 2}, {6, 1, 3}, {8, 2, 1}, {8, 2, 2}, {8, 2, 4},
-                               {6, 1, 1}, {3, 1, 1}, {4, 2, 1}, {2, 1, 1}, {2, 2, 1}};
-constexpr int kWindowedShape = 6;  // shape 6: (6, 1, 1) with the windowed schedule
-// shapes 7-10: several K chunks per stage: 2 (3 stages of 64 KB; a CTA pair: 4 stages of
+                               {3, 1, 1}, {4, 2, 1}, {2, 1, 1}, {2, 2, 1}};
+// shapes 6-9: several K chunks per stage: 2 (3 stages of 64 KB; a CTA pair: 4 stages of
 // 48 KB), 3 (2 stages of 96 KB), 4 (a CTA pair: 2 stages of 96 KB)
 constexpr int kNumCfg = 2 * (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 std::atomic<int> g_cfg{18};
 
 bool tc_bits_ok(int bits) { return bits == 40 || bits == 48 || bits == 56; }
 
-bool tc_plan(int K, int bits, int* beta, int* S, int* parts, int max_parts) {
-  // Slices of beta bits, S = ceil(bits / beta) (beta S <= 60, S <= kMaxS), and the number of K
-  // parts such that every group of one order over one part sums to an integer below 2^24 and
-  // stays exact in FP32: 2 Kpart 2^(2 beta) (1 + (S - 2) / 4) <= 2^24 (the top digits reach
-  // 2^beta, the others 2^(beta - 1)).  The widest beta whose parts fit max_parts and whose
-  // schedule fits the kernel's item table wins (fewest slice products).  When no width from 8
-  // down to 4 covers K, false is returned (the placeholder plan must not be launched).
+bool tc_plan(int K, int bits, int max_parts, TcPlan* out) {
+  // Digits of beta bits, S = ceil(bits / beta) slices (beta S - 1 >= bits - 1 bits below the line
+  // maximum, beta S <= 60, S <= kMaxS): every digit has |q| <= 2^(beta - 1), so a slice product
+  // is an integer multiple of its order's unit of magnitude <= 2^(2 beta - 2), and a group of
+  // gsize products of one order over a K part of Kp real terms is exact in FP32 when
+  // gsize Kp 2^(2 beta - 2) <= 2^24.  Among the feasible (beta, parts, gsize) the plan with the
+  // least estimated time wins: every group costs max(its MMA work, one accumulator flush), with
+  // the work counted in products x K chunks and a flush worth about 8 of those (the epilogue
+  // adds each group into the TMEM-resident sums while the MMAs fill the other accumulator).
+  // False when no digit width from 8 down to 4 covers K within max_parts parts and the kernel's
+  // item table (the placeholder plan must not be launched).
+  constexpr double kFlush = 8.0;
   const int nch = std::max(1, (2 * K + kKC - 1) / kKC);
+  double best = -1.0;
   if (tc_bits_ok(bits)) {
     for (int b = 8; b >= 4; --b) {
       const int s = (bits + b - 1) / b;
       if (s > kMaxS || b * s > 60) continue;
-      const double grow = 1.0 + std::max(0, s - 2) / 4.0;
-      const double kmax = 16777216.0 / (std::ldexp(1.0, 2 * b) * grow);  // real terms per part
-      const int chunks_per_part = (int)std::floor(kmax / kKC);
-      if (chunks_per_part < 1) continue;
-      const int np = (nch + chunks_per_part - 1) / chunks_per_part;
-      if (np <= std::min(max_parts, kMaxParts) && (long long)np * s * (s + 1) / 2 <= kMaxItems) {
-        *beta = b;
-        *S = s;
-        *parts = np;
-        return true;
+      const double per = std::ldexp(1.0, 2 * b - 2);                   // |q_s q_t| bound
+      const int cpp = (int)std::floor(16777216.0 / per / kKC);         // chunks per part, gsize 1
+      if (cpp < 1) continue;
+      const int np = (nch + cpp - 1) / cpp;
+      if (np > std::min(max_parts, kMaxParts) || (long long)np * s * (s + 1) / 2 > kMaxItems)
+        continue;
+      const int part_ch = (nch + np - 1) / np;                          // longest part
+      const int gs = std::max(1, (int)std::floor(16777216.0 / (per * part_ch * kKC)));
+      double cost = 0.0;
+      for (int d = 1; d <= s; ++d)
+        for (int left = d; left > 0; left -= gs)
+          cost += std::max((double)std::min(left, gs) * part_ch, kFlush);
+      cost *= np;
+      if (best < 0.0 || cost < best) {
+        best = cost;
+        *out = TcPlan{b, s, np, gs};
       }
     }
   }
-  *beta = 4;
-  *S = kMaxS;
-  *parts = 1;
+  if (best >= 0.0) return true;
+  *out = TcPlan{4, kMaxS, 1, 1};
   return false;
 }
 
 bool tc_supports_k(int K, int bits) {
-  int b, s, p;
-  return K >= 1 && tc_plan(K, bits, &b, &s, &p, 4) && tc_plan(K, bits, &b, &s, &p, 8);
+  TcPlan pl;
+  return K >= 1 && tc_plan(K, bits, 4, &pl) && tc_plan(K, bits, 8, &pl);
 }
 
 
@@ -895,6 +786,19 @@ __global__ void k_flag_timeout(const int32_t* err, int P, int32_t* status) {
   if (p < P && *err) atomicOr(status + p, NEGF_PT_TIMEOUT);
 }
 }  // namespace
+
+cudaError_t tc_prof_flops(double* alg, double* hw) {
+  double v[2] = {0.0, 0.0};
+  cudaError_t e = cudaMemcpyFromSymbol(v, g_tc_prof, sizeof(v));
+  *alg = v[0];
+  *hw = v[1];
+  return e;
+}
+
+cudaError_t tc_prof_reset() {
+  const double z[2] = {0.0, 0.0};
+  return cudaMemcpyToSymbol(g_tc_prof, z, sizeof(z));
+}
 
 cudaError_t tc_timeout_reset(cudaStream_t s, const TcWs& ws) {
   return cudaMemsetAsync(ws.err, 0, sizeof(int32_t), s);
@@ -919,9 +823,9 @@ void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, int bits, 
   // change between sizing and use cannot overrun the workspace
   int S = 0;
   for (int mp : {4, 8}) {
-    int b2, s2, p2;
-    tc_plan(K, bits, &b2, &s2, &p2, mp);
-    S = std::max(S, s2);
+    TcPlan pl;
+    tc_plan(K, bits, mp, &pl);
+    S = std::max(S, pl.S);
   }
   const size_t L = (size_t)round_up(2 * K, kKC);
   auto take = [&](size_t bytes) -> void* {
@@ -966,9 +870,10 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
   const int32_t* actB = zmB == 0 ? active : nullptr;
   const int cfg = g_cfg.load();
   const int CG = kShapes[cfg / 2].cg;
-  int bta, S, parts;
-  if (!tc_plan(K, bits, &bta, &S, &parts, cfg % 2 == 0 ? 4 : 8))
+  TcPlan pl;
+  if (!tc_plan(K, bits, cfg % 2 == 0 ? 4 : 8, &pl))
     return cudaErrorInvalidValue;  // K beyond the exact range (callers check tc_supports_k)
+  const int bta = pl.beta, S = pl.S;
   const int L = round_up(2 * K, kKC);
   const int N2 = 2 * N;
   __nv_bfloat16* sa = static_cast<__nv_bfloat16*>(ws.slicesA);
@@ -987,11 +892,11 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
   CUtensorMap mA, mB;
   if (!make_map(&mA, sa, L, M, (long long)PA * S, kBM)) return cudaErrorInvalidValue;
   if (!make_map(&mB, sb, L, N2, (long long)PB * S, kNT / CG)) return cudaErrorInvalidValue;
+  if ((long long)pl.parts * S * (S + 1) / 2 > kMaxItems) return cudaErrorInvalidValue;
+  const Sched sc = build_sched(pl, L / kKC);
 #define NEGF_TC_ARGS                                                                          \
-  s, P, M, N2, K, L, S, 2 * bta, parts, mA, mB, ws, zA, zmA, zB, zmB, alpha, beta, gamma, C, D, \
+  s, P, M, N2, K, S, 2 * bta, sc, mA, mB, ws, zA, zmA, zB, zmB, alpha, beta, gamma, C, D,       \
       add_identity, trunc_a ? bta : 0, active, rmax
-  // the windowed schedule does not skip slice orders: truncated products take the plain one
-  if (cfg / 2 == kWindowedShape && !trunc_a) return launch_tc<kNT, 6, 1, 1, true>(NEGF_TC_ARGS);
   switch (cfg / 2) {
     case 0: return launch_tc<kNT, 6, 1, 1>(NEGF_TC_ARGS);
     case 1: return launch_tc<kNT, 6, 1, 2>(NEGF_TC_ARGS);
@@ -999,10 +904,10 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
     case 3: return launch_tc<kNT, 8, 2, 1>(NEGF_TC_ARGS);
     case 4: return launch_tc<kNT, 8, 2, 2>(NEGF_TC_ARGS);
     case 5: return launch_tc<kNT, 8, 2, 4>(NEGF_TC_ARGS);
-    case 7: return launch_tc<kNT, 3, 1, 1, false, 2>(NEGF_TC_ARGS);
-    case 8: return launch_tc<kNT, 4, 2, 1, false, 2>(NEGF_TC_ARGS);
-    case 9: return launch_tc<kNT, 2, 1, 1, false, 3>(NEGF_TC_ARGS);
-    case 10: return launch_tc<kNT, 2, 2, 1, false, 4>(NEGF_TC_ARGS);
+    case 6: return launch_tc<kNT, 3, 1, 1, 2>(NEGF_TC_ARGS);
+    case 7: return launch_tc<kNT, 4, 2, 1, 2>(NEGF_TC_ARGS);
+    case 8: return launch_tc<kNT, 2, 1, 1, 3>(NEGF_TC_ARGS);
+    case 9: return launch_tc<kNT, 2, 2, 1, 4>(NEGF_TC_ARGS);
     default: return launch_tc<kNT, 6, 1, 1>(NEGF_TC_ARGS);
   }
 #undef NEGF_TC_ARGS

@@ -32,10 +32,15 @@ bool tc_bits_ok(int bits);
 size_t tc_ws_bytes(int P, int M, int N, int K, int bits);
 void tc_ws_carve(char* base, size_t& off, int P, int M, int N, int K, int bits, TcWs& w);
 
-// Slices and exactness parameters for a contraction length K (complex) when at most max_parts
-// K parts may be accumulated as separate exact groups: digit width beta, slice count S
-// (beta S >= bits) and the number of parts.  False when no such plan exists.
-bool tc_plan(int K, int bits, int* beta, int* S, int* parts, int max_parts);
+// Slices and exactness parameters of a contraction: digit width beta, slice count S (values of
+// beta S - 1 >= bits - 1 bits), K split into `parts` and at most `gsize` slice products of one
+// order summed per exact FP32 accumulator group.
+struct TcPlan {
+  int beta, S, parts, gsize;
+};
+// The plan for a contraction length K (complex) when at most max_parts K parts may be used.
+// False when no exact plan exists.
+bool tc_plan(int K, int bits, int max_parts, TcPlan* out);
 // Whether the tensor-core GEMM covers K exactly under every configuration at `bits` bits per
 // value (48 bits: K <= 28032).
 bool tc_supports_k(int K, int bits);
@@ -45,6 +50,12 @@ bool tc_supports_k(int K, int bits);
 // NEGF_PT_TIMEOUT into status[0..P) when it is set.  Both are asynchronous on s.
 cudaError_t tc_timeout_reset(cudaStream_t s, const TcWs& ws);
 cudaError_t tc_timeout_flag(cudaStream_t s, const TcWs& ws, int P, int32_t* status);
+
+// Flops of the tensor-core GEMM launches made while profiling was on, counted on the device
+// for the items that ran (the current device; both calls synchronise it): algorithmic complex
+// 8 M N K, and the BF16 MMA flops issued over the padded tiles.
+cudaError_t tc_prof_flops(double* alg, double* hw);
+cudaError_t tc_prof_reset();
 
 // n_distinct: number of different matrices an indexed operand (idx != NULL) selects from
 // (0 = unknown: slice every item).  trunc_a: the product only needs to be accurate relative

@@ -22,7 +22,7 @@ __device__ __forceinline__ unsigned long long absbits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-// exponent e with max|x| < 2^e (0 for an all-zero row)
+// exponent e with max|x| < 2^e (0 for an all-zero row); the slicing uses e + 1
 __device__ __forceinline__ int scale_exp(double mx) {
   if (!(mx > 0.0)) return 0;
   int e;
@@ -30,12 +30,14 @@ __device__ __forceinline__ int scale_exp(double mx) {
   return e;
 }
 
-// Fixed-point slicing of one value.  x 2^(beta - e) (|x| < 2^e) is rounded once to the integer
-// R = round(|x| 2^(beta S - e)) < 2^(beta S) + 1 and written in balanced base-2^beta digits
-// q_0 .. q_{S-1} (value sum_s q_s 2^(-beta s)): q_0 in [0, 2^beta], q_s in [-2^(beta-1),
-// 2^(beta-1)) for s >= 1.  Adding H = 2^(beta-1) to every digit position below the top one turns
-// the balanced digits into plain bit fields of R + H (minus 2^(beta-1)), so each digit is a
-// constant shift and mask.  Every q_s 2^(-beta s) is exact in BF16.
+// Fixed-point slicing of one value.  The line exponent e is one above the line maximum's
+// (|x| < 2^(e - 1)), so x 2^(beta - e) is rounded once to the integer
+// R = round(|x| 2^(beta S - e)) <= 2^(beta S - 1) and written in balanced base-2^beta digits
+// q_0 .. q_{S-1} (value sum_s q_s 2^(-beta s)): q_0 in [0, 2^(beta-1)], q_s in [-2^(beta-1),
+// 2^(beta-1)) for s >= 1, so |q_s q_t| <= 2^(2 beta - 2) for every slice product.  Adding
+// H = 2^(beta-1) to every digit position below the top one turns the balanced digits into plain
+// bit fields of R + H (minus 2^(beta-1)), so each digit is a constant shift and mask.  Every
+// q_s 2^(-beta s) is exact in BF16.
 template <int BETA, int S>
 struct Digits {
   static constexpr int kBits = BETA * S;
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(256) k_slice(int n_lines, int K, int L, BMc<do
   __syncthreads();
   if (threadIdx.x < 32) {
     const int li = threadIdx.x, line = l0 + li;
-    const int e = scale_exp(__longlong_as_double((long long)smax[0][li]));
+    const int e = scale_exp(__longlong_as_double((long long)smax[0][li])) + 1;
     sexp[li] = e;
     if (line < n_lines) eo[(long long)p * n_lines + line] = e;
   }
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(256) k_slice_strip(int n_lines, int K, int L, 
       }
       m = warp_max(m);
       if (lane == 0) {
-        const int e = scale_exp(__longlong_as_double((long long)m));
+        const int e = scale_exp(__longlong_as_double((long long)m)) + 1;
         sexp[w] = e;
         if (l0 + w < n_lines) eo[(long long)p * n_lines + l0 + w] = e;
       }

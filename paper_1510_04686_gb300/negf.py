@@ -56,7 +56,7 @@ EXPORTS = ("negf_default_options", "negf_abi_version", "negf_status_string",
            "negf_profile_enable", "negf_profile_reset", "negf_profile_read", "negf_profile_flops",
            "negf_launch_count", "negf_zinv_batched_noalloc", "negf_tc_config_count",
            "negf_tc_config_set", "negf_tc_config_get", "negf_last_cuda_error",
-           "negf_fp64_fallback_count")
+           "negf_fp64_fallback_count", "negf_debug_fail_waits")
 
 
 def library():
@@ -124,6 +124,8 @@ def library():
     lib.negf_tc_config_get.restype = c_int32
     lib.negf_last_cuda_error.argtypes = []
     lib.negf_last_cuda_error.restype = ctypes.c_char_p
+    lib.negf_debug_fail_waits.argtypes = [c_int32]
+    lib.negf_debug_fail_waits.restype = None
     lib.negf_fp64_fallback_count.argtypes = []
     lib.negf_fp64_fallback_count.restype = ctypes.c_longlong
     _LIB = lib

@@ -139,16 +139,17 @@ def test_autotune_cache_rejects_stale_records(tmp_path):
 
 
 def test_mixed_form_rejects_contractions_beyond_its_exact_range(lib):
-    """The split-BF16 GEMM keeps 48-bit slices exact for contraction lengths up to 28032; longer
-    ones (blocks, GEMM K, inverse size) are refused on the host instead of losing accuracy."""
+    """The split-BF16 GEMM keeps 48-bit slices exact for contraction lengths up to 393216; longer
+    ones (GEMM K) are refused on the host instead of losing accuracy, and blocks beyond the
+    mixed inverse's range (n > 9266) are refused by every sweep entry point."""
     P = ctypes.c_void_p
     fake = P(16)
     mixed, fp64 = B.PREC_MIXED, B.PREC_FP64
-    assert lib.negf_zgemm_workspace_size(mixed, 1, 8, 8, 28032) > 0
-    assert lib.negf_zgemm_workspace_size(mixed, 1, 8, 8, 28033) == 0
-    assert lib.negf_zgemm_workspace_size(fp64, 1, 8, 8, 28033) > 0
-    r = lib.negf_zgemm_batched(mixed, 1, 8, 8, 30000, 1.0, 0.0, fake, 0, 30000, 0, fake, 0, 8, 0,
-                               0.0, 0.0, fake, 64, 8, fake, 1 << 40, None)
+    assert lib.negf_zgemm_workspace_size(mixed, 1, 8, 8, 393216) > 0
+    assert lib.negf_zgemm_workspace_size(mixed, 1, 8, 8, 393217) == 0
+    assert lib.negf_zgemm_workspace_size(fp64, 1, 8, 8, 393217) > 0
+    r = lib.negf_zgemm_batched(mixed, 1, 8, 8, 400000, 1.0, 0.0, fake, 0, 400000, 0, fake, 0, 8,
+                               0, 0.0, 0.0, fake, 64, 8, fake, 1 << 40, None)
     assert r == 8
     assert lib.negf_zinv_workspace_size(mixed, 1, 28033) == 0
     r = lib.negf_zinv_batched(mixed, 1, 28033, fake, fake, 2, fake, fake, 1 << 40, None)
@@ -191,9 +192,11 @@ def test_block_inverse_size_limits_are_checked_on_the_host(lib):
 
 def test_precision_tiers_and_their_exact_ranges(lib):
     """Each mixed tier keeps its fixed-point slices exact up to its own contraction length
-    (40 bits: K <= 43648, 48 bits: 28032, 56 bits: 7008) and refuses longer ones on the host; the
-    decimation's automatic precision is the 56-bit tier where it is exact, else the 48-bit one."""
-    for prec, kmax in ((B.PREC_MIXED_40, 43648), (B.PREC_MIXED, 28032), (B.PREC_MIXED_56, 7008)):
+    (40 bits: K <= 524288, 48 bits: 393216, 56 bits: 98304) and refuses longer ones on the host;
+    the decimation's automatic precision is the 56-bit tier where it is exact, else the 48-bit
+    one."""
+    for prec, kmax in ((B.PREC_MIXED_40, 524288), (B.PREC_MIXED, 393216),
+                       (B.PREC_MIXED_56, 98304)):
         assert lib.negf_zgemm_workspace_size(prec, 1, 8, 8, kmax) > 0
         assert lib.negf_zgemm_workspace_size(prec, 1, 8, 8, kmax + 1) == 0
     # 56-bit values need more slices: a larger workspace for the same product
@@ -208,9 +211,9 @@ def test_precision_tiers_and_their_exact_ranges(lib):
     l56 = negf.options(precision=B.PREC_MIXED, lead_precision=B.PREC_MIXED_56)
     size = lambda o, dv=d: lib.negf_workspace_size(ctypes.byref(dv), 8, ctypes.byref(o), B.WS_LEAD)
     assert size(auto) == size(l56) > size(l48) > 0
-    # beyond b = 7008 the automatic lead precision falls back to 48 bits
-    big = _dev(b=8000)
-    assert size(auto, big) == size(l48, big) > 0 and size(l56, big) == 0
+    # every block the mixed inverse takes (n <= 9266) is inside the 56-bit range
+    big = _dev(b=9266)
+    assert size(auto, big) == size(l56, big) > size(l48, big) > 0
     for bad in (dict(lead_precision=5), dict(lead_precision=-2), dict(refine_max=17),
                 dict(refine_max=-1)):
         o = negf.options(precision=B.PREC_MIXED, **bad)

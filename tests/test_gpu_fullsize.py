@@ -1,5 +1,11 @@
 """Parity at the benchmark's full size, in the launch configuration bench.py times.
 
+Two sources of expected values: two points of a 256-point batch checked element by element
+against the oracle run live, and the stored oracle values of tests/golden/c1_oracle.json (one
+whole k-slice of 512 energies: energy integrals of the per-atom density and bond currents, and
+per-point slab densities, currents and T at 48 + 16 energies including the bias window and the
+band edges) for every stored point.
+
 The device is the benchmark's: N = 70 slabs x 400 x 400 blocks (40 atoms x 10 orbitals), Si with
 p(Ge) = 0.1, transverse k-points with k-independent hoppings, eta = 1e-6 in leads and device.
 A batch of 256 (E, k) points is solved in one chunk (the bench's points per step) in the mixed
@@ -15,6 +21,8 @@ to the energy-integrated observables (tests in test_gpu_mixed.py); single points
 resonance of width eta amplify the GEMM error by the block condition number, which is why the
 per-point bar is looser.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -94,3 +102,70 @@ def test_fullsize_fp64_matches_oracle(workload):
         print(f"FP64 point {p}: density {en:.2e} current {ej:.2e} T {eT:.2e}")
         assert en < 2e-7 and ej < 2e-7
         assert eT < 2e-7 * max(1.0, abs(ref["transmission"]))
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c1_oracle.json")
+
+
+@pytest.mark.parametrize("sweep", ["mixed", "mixed_40"])
+def test_fullsize_kslice_matches_stored_oracle(sweep):
+    """The benchmark device's whole k-slice k = -3 pi / 8 (512 energies, two 256-point chunks)
+    plus 16 points of k = +3 pi / 8, in the mixed forms (56-bit lead decimation): the energy
+    integrals of the per-atom density and of the bond currents within 1e-6 of the oracle's
+    (the stated bar), and every stored point within the per-point bars -- slab density 1e-6,
+    bond current 1e-6 of the slice's largest current (outside the bias window j(E) = (f_L - f_R)
+    T(E) vanishes, so a point's own current is no scale), T within 1e-6 * max(1, T)."""
+    if not os.path.exists(GOLDEN):
+        pytest.skip("stored oracle values not generated")
+    import json
+    with open(GOLDEN) as fh:
+        gd = json.load(fh)
+    negf._build.build()
+    dev = make_device(N, B, SEED, ge_frac=0.1, with_k=True)
+    ks, _ = k_grid(N_K)
+    km, kp = gd["k_main"], gd["k_partner"]
+    Hd = np.stack([hamiltonian_k(dev, float(ks[k]))[0] for k in (km, kp)])
+    Hu = np.broadcast_to(dev.T, (2,) + dev.T.shape).copy()
+    d = negf.Device(torch.as_tensor(Hd, device="cuda"), torch.as_tensor(Hu, device="cuda"))
+    E_all, wE = energy_grid_linspace(-3.0, 3.0, N_E)
+    prec = negf.PREC_MIXED if sweep == "mixed" else negf.PREC_MIXED_40
+    opt = negf.options(precision=prec, chunk=P)
+    dens_int = torch.zeros((1, N * B), dtype=torch.float64, device="cuda")
+    cur_int = torch.zeros((1, N - 1), dtype=torch.float64, device="cuda")
+    T = np.empty(N_E)
+    per = {}
+    part = sorted(q["energy_index"] for q in gd["points"] if q["k_index"] == kp)
+    jobs = [(0, km, np.arange(s, s + P)) for s in range(0, N_E, P)] + [(1, kp, np.array(part))]
+    for sys_i, k, idx in jobs:
+        Et = torch.as_tensor(E_all[idx], device="cuda")
+        st = torch.full((len(idx),), sys_i, dtype=torch.int32, device="cuda")
+        lead = negf.lead_selfenergy(d, Et, st, opt)
+        r = negf.rgf_solve(d, Et, st, lead["sigma_R"], lead["sigma_L"], opt)
+        assert int(r["status"].abs().sum()) == 0 and int(lead["status"].abs().sum()) == 0
+        if sys_i == 0:
+            w = torch.as_tensor(wE[idx], device="cuda")
+            dens_int += negf.integrate(r["density"], w)
+            cur_int += negf.integrate(r["current"], w)
+            T[idx] = r["transmission"].cpu().numpy()
+        dn = r["density"].reshape(len(idx), N, B).sum(dim=2).cpu().numpy()
+        cu, tr = r["current"].cpu().numpy(), r["transmission"].cpu().numpy()
+        for q, e in enumerate(idx):
+            per[(k, int(e))] = (dn[q], cu[q], tr[q])
+    atoms = dens_int.reshape(-1, 10).sum(dim=1).cpu().numpy()
+    e_n = _rel(atoms, np.asarray(gd["integrated_atom_density_main"]))
+    e_j = _rel(cur_int.reshape(-1).cpu().numpy(), np.asarray(gd["integrated_current_main"]))
+    e_T = np.abs(T - np.asarray(gd["transmission_main"])).max()
+    print(f"{sweep}: integrated density {e_n:.2e} current {e_j:.2e}; T over the slice {e_T:.2e}")
+    assert e_n < 1e-6 and e_j < 1e-6
+    assert e_T < 1e-6 * max(1.0, np.abs(gd["transmission_main"]).max())
+    jscale = max(np.abs(q["current"]).max() for q in gd["points"] if q["k_index"] == km)
+    worst = [0.0, 0.0, 0.0]
+    for q in gd["points"]:
+        dn, cu, tr = per[(q["k_index"], q["energy_index"])]
+        en = _rel(dn, np.asarray(q["slab_density"]))
+        ej = np.abs(cu - np.asarray(q["current"])).max() / jscale
+        eT = abs(tr - q["transmission"]) / max(1.0, abs(q["transmission"]))
+        worst = [max(worst[0], en), max(worst[1], ej), max(worst[2], eT)]
+        assert en < 1e-6 and ej < 1e-6 and eT < 1e-6, (q["k_index"], q["energy_index"], en, ej, eT)
+    print(f"{sweep}: {len(gd['points'])} stored points, worst slab density {worst[0]:.2e} "
+          f"current {worst[1]:.2e} T {worst[2]:.2e}")

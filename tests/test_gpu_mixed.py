@@ -69,3 +69,51 @@ def test_mixed_config0_integrated_parity():
     eT = np.abs(r["transmission"] - T_ref).max()
     print(f"config0 mixed: density {en:.2e} current {ej:.2e} T {eT:.2e}")
     assert en < 1e-6 and ej < 1e-6 and eT < 1e-6
+
+
+def test_timeout_reaches_every_point_status():
+    """A bounded wait inside a tensor-core GEMM that gives up sets the GEMM's device error word;
+    the call then ORs NEGF_PT_TIMEOUT into the status of every point it was solving.  The word is
+    set here by the library's host-side test hook (no GPU wait expires), and the device path
+    that turns it into per-point status runs as in a real timeout."""
+    dev = make_device(3, 24, 77)
+    E = np.linspace(-1.0, 1.0, 5)
+    lib = negf.library()
+    opt = negf.options(precision=negf.PREC_MIXED)
+    try:
+        lib.negf_debug_fail_waits(1)
+        r = gpu_solve([dev.D], [dev.T], E, np.zeros(5, int), opt)
+    finally:
+        lib.negf_debug_fail_waits(0)
+    assert np.all(r["status"] & 16 == 16) and np.all(r["lead"]["status"] & 16 == 16)
+    r = gpu_solve([dev.D], [dev.T], E, np.zeros(5, int), opt)
+    assert np.all(r["status"] == 0) and np.all(r["lead"]["status"] == 0)
+    # the FP64 form has no bounded waits: the hook does not apply
+    try:
+        lib.negf_debug_fail_waits(1)
+        r = gpu_solve([dev.D], [dev.T], E, np.zeros(5, int), negf.options(precision=negf.PREC_FP64))
+    finally:
+        lib.negf_debug_fail_waits(0)
+    assert np.all(r["status"] == 0)
+
+
+@pytest.mark.parametrize("lead", [negf.PREC_MIXED_56, negf.PREC_FP64])
+@pytest.mark.parametrize("sweep", [negf.PREC_MIXED_40, negf.PREC_MIXED, negf.PREC_MIXED_56])
+def test_precision_tiers_match_oracle(lead, sweep):
+    """Sweep tiers with the 56-bit (default) or FP64 lead decimation on a device spanning several
+    GEMM tiles with a ragged tail (b = 150): per point within 1e-6 (40-bit sweep: 1e-5) of the
+    oracle, energy integrals within 1e-6.  (A 48-bit decimation misses the per-point bar on this
+    device: T is off by 1.5e-5 at one energy, the amplification the 56-bit default avoids.)"""
+    dev = make_device(5, 150, 616, ge_frac=0.1)
+    E = np.linspace(-1.9, 1.7, 9)
+    r = gpu_solve([dev.D], [dev.T], E, np.zeros(9, int),
+                  negf.options(precision=sweep, lead_precision=lead))
+    ref = oracle_solve([dev.D], [dev.T], E, [0] * 9, 1e-6, 1e-6)
+    bar = 1e-5 if sweep == negf.PREC_MIXED_40 else 1e-6
+    for p, o in enumerate(ref):
+        assert _rel(r["density"][p], o["density"]) < bar
+        assert abs(r["transmission"][p] - o["transmission"]) < bar * max(1.0, abs(o["transmission"]))
+    w = np.full(len(E), E[1] - E[0])
+    assert _rel(O.integrate(r["density"], w), O.integrate([o["density"] for o in ref], w)) < 1e-6
+    assert _rel(O.integrate(r["current"], w), O.integrate([o["current"] for o in ref], w)) < 1e-6
+    assert np.all(r["status"] == 0)

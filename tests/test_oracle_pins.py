@@ -401,3 +401,47 @@ def test_density_sum_rule_fixes_eq7_normalisation():
         n = sum(we * O.solve_point(dev.D, dev.T, e, 0.0, None, eta_lead=1e-12, mu_L=mu, mu_R=mu,
                                    kT=KT)["density"] for e, we in zip(E, wE))
         assert np.abs(n - expect).max() < 1e-9
+
+
+def test_integrate_is_the_trapezoid_rule_on_polynomials():
+    """Eq. 7's energy quadrature with trapezoid weights integrates 1 and E exactly and E^2 with
+    the closed-form trapezoid error h^2 (b - a) / 12 * 2 = h^2 on [-3, 3]; summation is in point
+    order with the weights applied once."""
+    from workloads import energy_grid_linspace
+    for n in (5, 64, 513):
+        E, w = energy_grid_linspace(-3.0, 3.0, n)
+        h = 6.0 / (n - 1)
+        vals = np.stack([np.ones(n), E, E ** 2, 2.0 * E ** 2 - 3.0], axis=1)
+        out = O.integrate(vals, w)
+        assert abs(out[0] - 6.0) < 1e-13
+        assert abs(out[1]) < 1e-13
+        assert abs(out[2] - (18.0 + h ** 2)) < 1e-12
+        assert abs(out[3] - (2.0 * (18.0 + h ** 2) - 18.0)) < 1e-12
+    # groups of points are integrated separately when the caller splits them
+    E, w = energy_grid_linspace(-1.0, 1.0, 9)
+    assert abs(O.integrate(np.ones((9, 1)), w)[0] - 2.0) < 1e-14
+
+
+def test_scba_mixing_is_linear_with_a_fixed_point():
+    """The Born update with linear mixing: Sigma <- (1 - m) Sigma_old + m Sigma_Born.  A Sigma_old
+    that is already the Born self-energy of the given G is a fixed point for every m (delta 0);
+    otherwise the step and the reported max |Delta Sigma| scale exactly with m."""
+    rng = np.random.default_rng(12)
+    n_k, n_E, n_orb = 2, 40, 5
+    dGR = rng.normal(size=(n_k, n_E, n_orb)) + 1j * rng.normal(size=(n_k, n_E, n_orb))
+    dGL = 1j * rng.random((n_k, n_E, n_orb))
+    wk = np.array([0.25, 0.75])
+    args = (dGR, dGL, wk, 0.01, 0.02, 12, O.bose(0.06, O.KT_300K))
+    bornR, bornL = O.scba_selfenergy(*args)
+    for m in (0.3, 1.0):
+        nR, nL, d = O.scba_step(*args, bornR, bornL, mix=m)
+        assert np.allclose(nR, bornR, atol=1e-15) and np.allclose(nL, bornL, atol=1e-15)
+        assert d < 1e-15
+    oldR = bornR + 0.1 * (rng.normal(size=bornR.shape) + 1j * rng.normal(size=bornR.shape))
+    oldL = bornL + 0.1j * rng.random(bornL.shape)
+    r1R, r1L, d1 = O.scba_step(*args, oldR, oldL, mix=1.0)
+    r3R, r3L, d3 = O.scba_step(*args, oldR, oldL, mix=0.3)
+    assert np.allclose(r1R, bornR) and np.allclose(r1L, bornL)
+    assert np.allclose(r3R - oldR, 0.3 * (bornR - oldR), atol=1e-14)
+    assert np.allclose(r3L - oldL, 0.3 * (bornL - oldL), atol=1e-14)
+    assert abs(d3 - 0.3 * d1) < 1e-14
