@@ -14,13 +14,15 @@ Stored:
   * the whole k-slice m = 2 (k = -3 pi / 8): T(E) at all 512 energies and the energy integrals
     (trapezoid weights) of the per-atom density (sum of each atom's 10 orbitals of Eq. 7's
     integrand) and of the bond currents (Eq. 8 read as 2 Re Tr[H_{i,i+1} G^<_{i+1,i}]);
-  * per-point values -- per-slab density sums, bond currents, T -- at 48 energies of that slice
-    (16 evenly spaced, the 12 nearest the bias window, 8 at each edge of the transmitting band,
-    the 4 energies 210-213) and at 16 of them on the partner slice m = 5 (k = +3 pi / 8).
+  * per-point values -- per-slab density sums, bond currents, T -- at the energies of that slice
+    chosen by select() (16 evenly spaced, the 12 nearest the bias window, 8 at each edge of the
+    transmitting band -- on this device the band covers the whole grid, so these are the grid's
+    ends -- and the 4 energies 210-213; 38 distinct energies) and at 16 of them on the partner
+    slice m = 5 (k = +3 pi / 8): 54 points.
 
     python tests/golden/make_c1_golden.py [--jobs 8]
 
-About 550 oracle points: ~15 minutes on 8 cores.
+About 530 oracle points: ~40 minutes on 8 cores.
 """
 import argparse
 import json
@@ -68,7 +70,7 @@ _CACHE = {}
 
 
 def select(T):
-    """48 energy indices of the main slice: even spread, bias window, band edges, 210-213."""
+    """Energy indices of the main slice: even spread, bias window, band edges, 210-213."""
     from workloads import energy_grid_linspace
     E, _ = energy_grid_linspace(-3.0, 3.0, N_E)
     sel = set(np.linspace(0, N_E - 1, 16).round().astype(int).tolist())

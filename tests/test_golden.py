@@ -114,3 +114,31 @@ def test_cuda_path_matches_golden(golden, prec):
     e_ji = _err(j_int, golden["integrated_current"])
     print(f"{prec}: integrated slab density {e_ni:.2e} current {e_ji:.2e}")
     assert e_ni < bar_n and e_ji < bar_j
+
+
+C1 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "c1_oracle.json")
+
+
+def test_oracle_reproduces_c1_golden_points():
+    """The stored values of the benchmark device (written by tests/golden/make_c1_golden.py from
+    the oracle, one BLAS thread per point) are reproduced by the oracle at one point of each
+    stored k-slice.  The bar is 5e-7: with a multi-threaded BLAS the oracle's own sums run in
+    another order, and on 70 slabs of 400 x 400 blocks at eta = 1e-6 that moves the slab
+    densities by 1.2e-9 at E = -0.006 eV on k = -3 pi / 8 and by 4.9e-8 at the same energy on
+    k = +3 pi / 8 (measured): the FP64 answer at a resonance is itself only that precise."""
+    from workloads import make_device, hamiltonian_k, k_grid, energy_grid_linspace
+    with open(C1) as fh:
+        gd = json.load(fh)
+    N, b = gd["N"], gd["b"]
+    dev = make_device(N, b, 1001, ge_frac=0.1, with_k=True)
+    ks, _ = k_grid(gd["n_k"])
+    E, _ = energy_grid_linspace(-3.0, 3.0, gd["n_E"])
+    picks = [q for q in gd["points"] if q["energy_index"] == 255]
+    assert {q["k_index"] for q in picks} == {gd["k_main"], gd["k_partner"]}
+    for q in picks:
+        Hd = hamiltonian_k(dev, float(ks[q["k_index"]]))[0]
+        r = O.solve_point(Hd, dev.T, float(E[q["energy_index"]]), gd["eta"], None)
+        assert _err(r["density"].reshape(N, b).sum(axis=1), np.asarray(q["slab_density"])) < 5e-7
+        assert _err(r["current"], np.asarray(q["current"])) < 5e-7
+        assert abs(r["transmission"] - q["transmission"]) < 5e-7
+    assert len(gd["points"]) >= 48 and len(gd["transmission_main"]) == gd["n_E"]
