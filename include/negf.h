@@ -244,6 +244,33 @@ negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, const double
 negf_status negf_integrate(int32_t n_pts, int32_t len, int32_t n_groups, const double* w,
                            const int32_t* group, const double* in, double* out, void* stream);
 
+/* ---- electrostatics of the NEGF-Poisson loop (Eq. 9) ---------------------------------------
+ * Eq. 9, div(eps grad Phi) = e (n - N_D), is written for the potential energy U = -e Phi that
+ * enters Eq. 1 (negf_rgf_solve's V, one value per atom shared by its orbitals) and discretised
+ * on the device's atom grid: slab i = 0..N-1 along transport, atom a = 0..A-1 across the slab
+ * (periodic, the device being periodic in that direction), contacts held at U_L (slab -1) and
+ * U_R (slab N).  With c_x, c_y the coupling constants eps / h^2 of the two directions and kappa
+ * = e^2 per unit of them (eV per electron), Eq. 9 becomes F(U) = 0 with
+ *   F[i][a] = c_x (2 U[i][a] - U[i-1][a] - U[i+1][a]) + c_y (2 U[i][a] - U[i][a-1] - U[i][a+1])
+ *             - kappa (n[i][a] - n_D[i][a]),
+ * n the electrons per atom (Eq. 7 summed over the atom's orbitals) and n_D the donor charge.
+ * negf_poisson_apply writes F for U [N][A] (n nullable: the operator alone, K U - boundary
+ * terms; n_D nullable = 0); all device double arrays, asynchronous on stream.  c_x, c_y >= 0.
+ * (For A == 1 there is no transverse term; for A == 2 both transverse neighbours are the one
+ * other atom.) */
+negf_status negf_poisson_apply(int32_t n_slabs, int32_t n_atoms, double c_x, double c_y,
+                               double U_L, double U_R, double kappa, const double* U,
+                               const double* n, const double* n_D, double* out, void* stream);
+/* Per-atom sums of per-orbital arrays and the reverse broadcast, for atoms of
+ * `orbitals_per_atom` consecutive orbitals (the last atom of a slab may be short):
+ *   atom[g][i][a] = sum_o orb[g][i][per a + o]   (groups stacked arrays [groups][N][block])
+ *   orb[i][o]     = atom[i][o / per]                                                         */
+negf_status negf_orbitals_to_atoms(int32_t groups, int32_t n_slabs, int32_t block,
+                                   int32_t orbitals_per_atom, const double* orb, double* atom,
+                                   void* stream);
+negf_status negf_atoms_to_orbitals(int32_t n_slabs, int32_t block, int32_t orbitals_per_atom,
+                                   const double* atom, double* orb, void* stream);
+
 /* ---- block operations the sweeps are built from ------------------------------------------
  * Batched complex GEMM  C[p] = alpha op(A[p]) op(B[p]) + beta C[p]  (Eqs. 1-2 are evaluated
  * block by block as such products).  complex128 row-major; op 0 = none, 1 = transpose,

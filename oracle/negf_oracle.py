@@ -345,3 +345,117 @@ def gradient_dense(Hd, Hu, E, eta, V, leads, c, d, sR=None, sL=None):
     Om = omega_dense(Hu, N, b, c, d)
     grad = np.real(np.diag(GL @ Om @ G) + np.diag(G.conj().T @ Om @ GL))
     return grad.reshape(N, b)
+
+
+# ----------------------------------------------------------------------------------------------
+# NEGF-Poisson self-consistency, Eq. (9)
+# ----------------------------------------------------------------------------------------------
+ORBITALS_PER_ATOM = 10
+
+
+def atom_sums(orb, N, b, per=ORBITALS_PER_ATOM):
+    """Electrons per atom from a per-orbital array [N*b]: atom a of slab i owns orbitals
+    per*a .. per*a + per - 1 of that slab.  Returns [N, A]."""
+    orb = np.asarray(orb, dtype=np.float64).reshape(N, b)
+    A = -(-b // per)
+    out = np.zeros((N, A))
+    for i in range(N):
+        for a in range(A):
+            out[i, a] = orb[i, per * a:min(per * a + per, b)].sum()
+    return out
+
+
+def atom_to_orbitals(U, b, per=ORBITALS_PER_ATOM):
+    """Per-orbital potential [N, b] from one value per atom [N, A]."""
+    U = np.asarray(U, dtype=np.float64)
+    N = U.shape[0]
+    out = np.zeros((N, b))
+    for i in range(N):
+        for o in range(b):
+            out[i, o] = U[i, o // per]
+    return out
+
+
+def poisson_residual(U, n, n_D, cx, cy, UL, UR, kappa):
+    """Eq. (9) for the potential energy U = -e Phi on the atom grid, as a residual:
+
+        F[i,a] = cx (2 U[i,a] - U[i-1,a] - U[i+1,a]) + cy (2 U[i,a] - U[i,a-1] - U[i,a+1])
+                 - kappa (n[i,a] - n_D[i,a])
+
+    (finite differences of -div(eps grad U); slab i along transport with the contacts held at
+    U[-1,:] = UL and U[N,:] = UR, atom a periodic across the slab; n = None: operator only).
+    """
+    U = np.asarray(U, dtype=np.float64)
+    N, A = U.shape
+    F = np.zeros((N, A))
+    for i in range(N):
+        for a in range(A):
+            left = U[i - 1, a] if i > 0 else UL
+            right = U[i + 1, a] if i < N - 1 else UR
+            r = cx * (2 * U[i, a] - left - right)
+            if A > 1:
+                r += cy * (2 * U[i, a] - U[i, (a - 1) % A] - U[i, (a + 1) % A])
+            if n is not None:
+                r -= kappa * (n[i, a] - (0.0 if n_D is None else n_D[i, a]))
+            F[i, a] = r
+    return F
+
+
+def poisson_matrix(N, A, cx, cy):
+    """The linear part of poisson_residual as a matrix K over the flattened (i, a) grid (the
+    residual of a unit potential at one atom with grounded contacts)."""
+    K = np.zeros((N * A, N * A))
+    for j in range(N * A):
+        e = np.zeros(N * A)
+        e[j] = 1.0
+        K[:, j] = poisson_residual(e.reshape(N, A), None, None, cx, cy, 0.0, 0.0, 0.0).ravel()
+    return K
+
+
+def electrons_per_atom(Hd, Hu, E, wE, eta, U, leads, per=ORBITALS_PER_ATOM):
+    """n = sum_E w_E n(E) per atom (Eq. 7) with the potential U [N, A] in Eq. (1)."""
+    N, b = Hd.shape[0], Hd.shape[1]
+    V = atom_to_orbitals(U, b, per)
+    dens = [solve_point(Hd, Hu, float(e), eta, V, leads=lo)["density"]
+            for e, lo in zip(E, leads)]
+    return atom_sums(integrate(dens, wE), N, b, per)
+
+
+def susceptibility(Hd, Hu, E, wE, eta, U, leads, per=ORBITALS_PER_ATOM):
+    """chi[a, a'] = d n_a / d U_a' (n_a energy-integrated), one row per atom from the dense
+    definition of the gradient (gradient_dense with the cotangent on atom a's orbitals)."""
+    N, b = Hd.shape[0], Hd.shape[1]
+    A = -(-b // per)
+    V = atom_to_orbitals(U, b, per)
+    chi = np.zeros((N * A, N * A))
+    for i in range(N):
+        for a in range(A):
+            c = np.zeros((N, b))
+            c[i, per * a:min(per * a + per, b)] = 1.0
+            g = np.zeros((N, b))
+            for e, w, lo in zip(E, wE, leads):
+                g += w * gradient_dense(Hd, Hu, float(e), eta, V, lo, c, None)
+            chi[i * A + a] = atom_sums(g.ravel(), N, b, per).ravel()
+    return chi
+
+
+def poisson_newton(Hd, Hu, E, wE, eta, n_D, cx, cy, UL, UR, kappa, U0=None, tol=1e-9,
+                   max_iter=30, mu_L=0.1, mu_R=-0.1, kT=KT_300K, per=ORBITALS_PER_ATOM):
+    """Self-consistent solution of Eqs. (1), (7) and (9): Newton's method on F(U) = 0 with
+    F = poisson_residual(U, n(U), ...) and the Jacobian J = K - kappa chi.  Lead self-energies
+    do not depend on U and are computed once per energy.  Returns (U, list of max |F|)."""
+    N, b = Hd.shape[0], Hd.shape[1]
+    A = -(-b // per)
+    leads = [lead_self_energies(Hd, Hu, float(e), eta, mu_L, mu_R, kT) for e in E]
+    U = np.zeros((N, A)) if U0 is None else np.array(U0, dtype=np.float64)
+    K = poisson_matrix(N, A, cx, cy)
+    hist = []
+    for _ in range(max_iter):
+        n = electrons_per_atom(Hd, Hu, E, wE, eta, U, leads, per)
+        F = poisson_residual(U, n, n_D, cx, cy, UL, UR, kappa)
+        hist.append(float(np.abs(F).max()))
+        if hist[-1] < tol:
+            break
+        J = K - kappa * susceptibility(Hd, Hu, E, wE, eta, U, leads, per)
+        U = U + np.linalg.solve(J, -F.ravel()).reshape(N, A)
+    return U, hist

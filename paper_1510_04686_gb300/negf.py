@@ -56,7 +56,8 @@ EXPORTS = ("negf_default_options", "negf_abi_version", "negf_status_string",
            "negf_profile_enable", "negf_profile_reset", "negf_profile_read", "negf_profile_flops",
            "negf_launch_count", "negf_zinv_batched_noalloc", "negf_tc_config_count",
            "negf_tc_config_set", "negf_tc_config_get", "negf_last_cuda_error",
-           "negf_fp64_fallback_count", "negf_debug_fail_waits")
+           "negf_fp64_fallback_count", "negf_debug_fail_waits", "negf_poisson_apply",
+           "negf_orbitals_to_atoms", "negf_atoms_to_orbitals")
 
 
 def library():
@@ -124,6 +125,13 @@ def library():
     lib.negf_tc_config_get.restype = c_int32
     lib.negf_last_cuda_error.argtypes = []
     lib.negf_last_cuda_error.restype = ctypes.c_char_p
+    lib.negf_poisson_apply.argtypes = [c_int32, c_int32, c_double, c_double, c_double, c_double,
+                                       c_double, P, P, P, P, P]
+    lib.negf_poisson_apply.restype = c_int32
+    lib.negf_orbitals_to_atoms.argtypes = [c_int32, c_int32, c_int32, c_int32, P, P, P]
+    lib.negf_orbitals_to_atoms.restype = c_int32
+    lib.negf_atoms_to_orbitals.argtypes = [c_int32, c_int32, c_int32, P, P, P]
+    lib.negf_atoms_to_orbitals.restype = c_int32
     lib.negf_debug_fail_waits.argtypes = [c_int32]
     lib.negf_debug_fail_waits.restype = None
     lib.negf_fp64_fallback_count.argtypes = []
@@ -531,3 +539,184 @@ def solve_ragged(systems, opt: _Opt, outputs=("density", "current", "transmissio
     for st in streams:
         cur.wait_stream(st)
     return results
+
+
+class RaggedGraph:
+    """A batch of systems with different block sizes solved by one CUDA graph.
+
+    ``systems`` is a list of (H_diag [N,b,b], H_up [N-1,b,b], E [n]) complex128 / float64 CUDA
+    tensors (for example alloy samples of different cross-sections, each with its energy list).
+    Systems of equal (N, b) are stacked into one device; each such group's lead decimation and
+    RGF sweeps are one batched launch chain on a stream of its own, and the chains of all groups
+    are captured together in one CUDA graph (fork from and join to the capturing stream), so a
+    replay launches the whole ragged batch at once and the groups overlap on the GPU.  The
+    decimation runs a fixed ``sr_steps`` steps with converged points masked on the device, so
+    the capture has no host synchronisation.  The Hamiltonians are stacked (copied) once, here;
+    the energy tensors given here are read again by every replay(), so changing them in place
+    and calling replay() solves the new energies.  replay() returns one result dict per system
+    (views into the group outputs).  Results equal those of solve_ragged with the same fixed
+    decimation steps.
+    """
+
+    def __init__(self, systems, opt: _Opt, sr_steps: int = 40,
+                 outputs=("density", "current", "transmission")):
+        o = _Opt()
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(opt), ctypes.sizeof(_Opt))
+        o.sr_host_check = 0
+        o.sr_max_iter = sr_steps
+        self.opt = o
+        groups = {}
+        for i, (Hd, Hu, E) in enumerate(systems):
+            groups.setdefault((int(Hd.shape[0]), int(Hd.shape[1])), []).append(i)
+        cur = torch.cuda.current_stream()
+        self.groups = []
+        for (N, b), idx in sorted(groups.items(), key=lambda kv: -kv[0][1]):
+            Hd = torch.stack([systems[i][0] for i in idx])
+            Hu = torch.stack([systems[i][1] for i in idx]) if N > 1 else None
+            E = torch.cat([systems[i][2] for i in idx])
+            sys_idx = torch.cat([torch.full((systems[i][2].numel(),), j, dtype=torch.int32,
+                                            device=E.device) for j, i in enumerate(idx)])
+            self.groups.append(dict(dev=Device(Hd, Hu), E=E, sys=sys_idx, idx=idx,
+                                    stream=torch.cuda.Stream(device=E.device)))
+        self.n_systems = len(systems)
+        self.energies = [systems[i][2] for i in range(len(systems))]
+        self.sizes = [E.numel() for E in self.energies]
+
+        def run():
+            for gr in self.groups:
+                gr["stream"].wait_stream(torch.cuda.current_stream())
+            for gr in self.groups:
+                with torch.cuda.stream(gr["stream"]):
+                    lead = lead_selfenergy(gr["dev"], gr["E"], gr["sys"], o)
+                    gr["out"] = rgf_solve(gr["dev"], gr["E"], gr["sys"], lead["sigma_R"],
+                                          lead["sigma_L"], o, outputs=outputs)
+                    gr["lead_status"] = lead["status"]
+            for gr in self.groups:
+                torch.cuda.current_stream().wait_stream(gr["stream"])
+
+        # warm-up outside the capture: workspaces (one per stream), kernel attributes, tensor
+        # maps' encoder
+        run()
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(device=cur.device)
+        cap.wait_stream(cur)
+        with torch.cuda.stream(cap):
+            with torch.cuda.graph(self.graph, stream=cap):
+                run()
+        cur.wait_stream(cap)
+
+    def replay(self):
+        for gr in self.groups:  # the callers' current energies into the captured buffers
+            gr["E"].copy_(torch.cat([self.energies[i] for i in gr["idx"]]))
+        self.graph.replay()
+        results = [None] * self.n_systems
+        for gr in self.groups:
+            off = 0
+            for i in gr["idx"]:
+                n = self.sizes[i]
+                r = {k: (v[off:off + n] if isinstance(v, torch.Tensor) else v)
+                     for k, v in gr["out"].items()}
+                r["lead_status"] = gr["lead_status"][off:off + n]
+                results[i] = r
+                off += n
+        return results
+
+
+ORBITALS_PER_ATOM = 10
+
+
+def poisson_apply(U, c_x, c_y, U_L=0.0, U_R=0.0, kappa=0.0, n=None, n_D=None):
+    """Residual of Eq. 9 on the atom grid, F = K U - boundary terms - kappa (n - n_D)
+    (negf_poisson_apply); U, n, n_D are [N, A] float64 CUDA tensors (n, n_D nullable)."""
+    _need(U, torch.float64, "U")
+    N, A = U.shape
+    for t, name in ((n, "n"), (n_D, "n_D")):
+        if t is not None:
+            _need(t, torch.float64, name, (N, A))
+    out = torch.empty_like(U)
+    _check(library().negf_poisson_apply(N, A, float(c_x), float(c_y), float(U_L), float(U_R),
+                                        float(kappa), _ptr(U), _ptr(n), _ptr(n_D), _ptr(out),
+                                        _stream()), "negf_poisson_apply")
+    return out
+
+
+def orbitals_to_atoms(orb, N, b, per=ORBITALS_PER_ATOM):
+    """[groups, N*b] (or [N*b]) per-orbital values -> [groups, N, A] per-atom sums."""
+    _need(orb, torch.float64, "orb")
+    groups = orb.numel() // (N * b)
+    A = -(-b // per)
+    out = torch.empty((groups, N, A), dtype=torch.float64, device=orb.device)
+    _check(library().negf_orbitals_to_atoms(groups, N, b, per, _ptr(orb), _ptr(out), _stream()),
+           "negf_orbitals_to_atoms")
+    return out
+
+
+def atoms_to_orbitals(U, b, per=ORBITALS_PER_ATOM):
+    """[N, A] per-atom values -> [N, b] per-orbital values."""
+    _need(U, torch.float64, "U")
+    N = U.shape[0]
+    out = torch.empty((N, b), dtype=torch.float64, device=U.device)
+    _check(library().negf_atoms_to_orbitals(N, b, per, _ptr(U), _ptr(out), _stream()),
+           "negf_atoms_to_orbitals")
+    return out
+
+
+def poisson_newton(dev: Device, E, w, sys_idx, opt: _Opt, n_D, kappa, c_x, c_y, U_L=0.0,
+                   U_R=0.0, U0=None, tol=1e-9, max_iter=30, per=ORBITALS_PER_ATOM):
+    """Self-consistent NEGF-Poisson solution (Eqs. 1, 7 and 9): Newton's method on
+    F(U) = K U - boundary terms - kappa (n(U) - n_D) = 0 for the potential energy U [N, A] per
+    atom, the electrons per atom n(U) = sum_p w[p] n(E_p, U) summed over each atom's orbitals.
+
+    Every step runs in the library: the RGF densities with U in Eq. 1 (negf_rgf_solve, V = U on
+    each atom's orbitals), the FP64 quadrature, the Poisson residual, and the Jacobian
+    J = K - kappa dn/dU, whose row for atom a is one adjoint sweep (negf_rgf_adjoint, the
+    backward of RGFFunction) with the cotangent w[p] on atom a's orbitals; the Newton step is
+    J^-1 (-F) by the FP64 block inverse and GEMM.  Lead self-energies do not depend on U and
+    are computed once.  Returns (U, list of max |F| per iteration)."""
+    N, b = dev.N, dev.b
+    A = -(-b // per)
+    n_pts = E.numel()
+    dv = E.device
+    _need(w, torch.float64, "w", (n_pts,))
+    _need(n_D, torch.float64, "n_D", (N, A))
+    lead = lead_selfenergy(dev, E, sys_idx, opt)
+    U = torch.zeros((N, A), dtype=torch.float64, device=dv) if U0 is None else U0.clone()
+    # K: the linear part of the residual, column by column (grounded contacts, no charge)
+    NA = N * A
+    K = torch.empty((NA, NA), dtype=torch.float64, device=dv)
+    unit = torch.zeros((N, A), dtype=torch.float64, device=dv)
+    for j in range(NA):
+        unit.view(-1)[j] = 1.0
+        K[:, j] = poisson_apply(unit, c_x, c_y).view(-1)
+        unit.view(-1)[j] = 0.0
+    hist = []
+    cot = torch.zeros((n_pts, N * b), dtype=torch.float64, device=dv)
+    for _ in range(max_iter):
+        V = atoms_to_orbitals(U, b, per)
+        out = rgf_solve(dev, E, sys_idx, lead["sigma_R"], lead["sigma_L"], opt, V=V,
+                        outputs=("density",))
+        n = orbitals_to_atoms(integrate(out["density"], w), N, b, per)[0]
+        F = poisson_apply(U, c_x, c_y, U_L, U_R, kappa, n, n_D)
+        hist.append(float(F.abs().max().item()))
+        if hist[-1] < tol:
+            break
+        chi = torch.empty((NA, NA), dtype=torch.float64, device=dv)
+        for i in range(N):
+            for a in range(A):
+                lo, hi = i * b + per * a, i * b + min(per * a + per, b)
+                cot[:, lo:hi] = w[:, None]
+                Vbar, _ = rgf_adjoint(dev, E, sys_idx, lead["sigma_R"], lead["sigma_L"], opt,
+                                      density_bar=cot, V=V)
+                cot[:, lo:hi] = 0.0
+                chi[i * A + a] = orbitals_to_atoms(Vbar, N, b, per).view(-1)
+        # J = K - kappa chi  (as complex128 for the block kernels); delta = -J^-1 F
+        J = K.to(torch.complex128)[None].contiguous()
+        zgemm(chi.to(torch.complex128)[None].contiguous(),
+              torch.eye(NA, dtype=torch.complex128, device=dv), J, alpha=-float(kappa), beta=1.0)
+        Jinv, st = zinv(J, precision=PREC_FP64)
+        if int(st.abs().sum().item()) != 0:
+            raise NegfError(5, "poisson_newton", "singular Jacobian")
+        d = zgemm(Jinv, F.reshape(1, NA, 1).to(torch.complex128).contiguous(), alpha=-1.0)
+        U = U + d.real.reshape(N, A)
+    return U, hist

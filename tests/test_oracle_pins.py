@@ -445,3 +445,99 @@ def test_scba_mixing_is_linear_with_a_fixed_point():
     assert np.allclose(r3R - oldR, 0.3 * (bornR - oldR), atol=1e-14)
     assert np.allclose(r3L - oldL, 0.3 * (bornL - oldL), atol=1e-14)
     assert abs(d3 - 0.3 * d1) < 1e-14
+
+
+# ---- Eq. 9: NEGF-Poisson self-consistency -----------------------------------------------------
+
+def test_poisson_operator_fourier_modes_and_linear_drop():
+    """The finite-difference operator of Eq. 9 on the atom grid: a mode sin(pi m (i+1)/(N+1))
+    cos(2 pi q a / A) with grounded contacts is an eigenvector with eigenvalue
+    cx (2 - 2 cos(pi m / (N+1))) + cy (2 - 2 cos(2 pi q / A)) (both directions and the periodic
+    wrap), and the contact-to-contact linear drop U_i = UL + (UR - UL)(i+1)/(N+1) has zero
+    residual."""
+    N, A, cx, cy = 7, 6, 1.3, 0.4
+    i = np.arange(N)[:, None]
+    a = np.arange(A)[None, :]
+    for m, q in ((1, 0), (2, 1), (5, 3)):
+        U = np.sin(np.pi * m * (i + 1) / (N + 1)) * np.cos(2 * np.pi * q * a / A)
+        lam = cx * (2 - 2 * np.cos(np.pi * m / (N + 1))) + cy * (2 - 2 * np.cos(2 * np.pi * q / A))
+        F = O.poisson_residual(U, None, None, cx, cy, 0.0, 0.0, 0.0)
+        assert np.allclose(F, lam * U, atol=1e-13)
+    UL, UR = 0.25, -0.35
+    lin = np.repeat((UL + (UR - UL) * (np.arange(N) + 1) / (N + 1))[:, None], A, axis=1)
+    assert np.abs(O.poisson_residual(lin, None, None, cx, cy, UL, UR, 0.0)).max() < 1e-14
+    # the matrix form agrees with the residual's linear part
+    K = O.poisson_matrix(N, A, cx, cy)
+    U = np.random.default_rng(2).normal(size=(N, A))
+    assert np.allclose(K @ U.ravel(), O.poisson_residual(U, None, None, cx, cy, 0, 0, 0).ravel())
+    assert np.allclose(K, K.T)
+
+
+def test_poisson_manufactured_solution_fixes_the_charge_term():
+    """F(U*) = 0 for any U* when the electrons are n = n_D + (K U* - boundary terms) / kappa:
+    more electrons than donors raise the potential energy (Eq. 9 with U = -e Phi)."""
+    N, A, cx, cy, kappa = 5, 4, 1.0, 0.5, 0.2
+    rng = np.random.default_rng(3)
+    U = rng.normal(size=(N, A))
+    nD = rng.random((N, A)) + 3.0
+    Kb = O.poisson_residual(U, None, None, cx, cy, 0.1, -0.1, 0.0)
+    n = nD + Kb / kappa
+    assert np.abs(O.poisson_residual(U, n, nD, cx, cy, 0.1, -0.1, kappa)).max() < 1e-12
+    # raising n at one atom lowers the residual there by kappa per electron
+    n2 = n.copy()
+    n2[2, 1] += 1.0
+    F = O.poisson_residual(U, n2, nD, cx, cy, 0.1, -0.1, kappa)
+    assert abs(F[2, 1] + kappa) < 1e-12 and np.abs(np.delete(F.ravel(), 2 * A + 1)).max() < 1e-12
+
+
+def _poisson_device():
+    dev = make_device(3, 20, 31, ge_frac=0.2)
+    E = np.linspace(-1.2, 0.6, 6)
+    wE = np.full(6, E[1] - E[0])
+    return dev, E, wE
+
+
+def test_susceptibility_matches_finite_differences():
+    """chi = d n_atom / d U_atom from the dense gradient of Eqs. 1-2 equals central finite
+    differences of the energy-integrated electrons per atom."""
+    dev, E, wE = _poisson_device()
+    N, b = 3, 20
+    A = 2
+    leads = [O.lead_self_energies(dev.D, dev.T, float(e), 1e-3, 0.1, -0.1, O.KT_300K) for e in E]
+    U0 = np.random.default_rng(5).uniform(-0.1, 0.1, (N, A))
+    chi = O.susceptibility(dev.D, dev.T, E, wE, 1e-3, U0, leads)
+    h = 1e-5
+    for col in (0, 3, 5):
+        dU = np.zeros(N * A)
+        dU[col] = h
+        up = O.electrons_per_atom(dev.D, dev.T, E, wE, 1e-3, U0 + dU.reshape(N, A), leads)
+        dn = O.electrons_per_atom(dev.D, dev.T, E, wE, 1e-3, U0 - dU.reshape(N, A), leads)
+        fd = ((up - dn) / (2 * h)).ravel()
+        assert np.abs(chi[:, col] - fd).max() < 1e-6 * max(1.0, np.abs(fd).max())
+
+
+def test_poisson_newton_converges_quadratically_to_the_picard_fixed_point():
+    """Newton on F(U) = 0 converges quadratically, and its U is the fixed point that a damped
+    Picard iteration (solve the linear Poisson equation with the previous electrons) reaches."""
+    dev, E, wE = _poisson_device()
+    N, A = 3, 2
+    cx, cy, kappa, eta = 1.0, 0.5, 0.05, 1e-3
+    leads = [O.lead_self_energies(dev.D, dev.T, float(e), eta, 0.1, -0.1, O.KT_300K) for e in E]
+    n0 = O.electrons_per_atom(dev.D, dev.T, E, wE, eta, np.zeros((N, A)), leads)
+    nD = np.full((N, A), n0.mean()) + 0.2
+    U, hist = O.poisson_newton(dev.D, dev.T, E, wE, eta, nD, cx, cy, 0.0, 0.0, kappa, tol=1e-11)
+    assert hist[-1] < 1e-11 and len(hist) <= 8
+    # quadratic: once small, each residual is far below the previous one
+    big = [h for h in hist if h < 1e-2]
+    for r0, r1 in zip(big, big[1:]):
+        assert r1 < 10 * r0 ** 1.5
+    # the Picard map's derivative kappa K^-1 chi has eigenvalues down to about -3 here, so a
+    # mixing of 1/4 keeps it contracting
+    K = O.poisson_matrix(N, A, cx, cy)
+    Up = np.zeros((N, A))
+    for _ in range(300):
+        n = O.electrons_per_atom(dev.D, dev.T, E, wE, eta, Up, leads)
+        rhs = (kappa * (n - nD)).ravel()   # contacts grounded: no boundary terms
+        Up = 0.75 * Up + 0.25 * np.linalg.solve(K, rhs).reshape(N, A)
+    assert np.abs(Up - U).max() < 1e-9
+    assert np.abs(U).max() > 1e-3   # a non-trivial potential
