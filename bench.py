@@ -32,10 +32,12 @@ WORK = dict(N=70, b=400, n_E=512, n_k=8, ge_frac=0.1, eta=1e-6, seed=1001,
 METRIC = "RGF energy-points/s (leads + forward/backward sweeps + observables + FP64 quadrature)"
 PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0)
 # DRAM bytes (read + write) of k_tc_gemm per 400 x 400 x 400 complex item from an ncu capture of
-# a 64-item launch of tensor-core configuration TC_PROFILED_CONFIG, scaled by the items of a
-# launch; None while the kernel has changed since the capture (the line then reports null).
-TC_DRAM_BYTES_PER_ITEM_B400 = None
-TC_PROFILED_CONFIG = 20
+# a 64-item 48-bit launch of tensor-core configuration 18 (806.6 MB read + 149.5 MB written),
+# scaled by the items of a launch; None once the kernel has changed since the capture (the line
+# then reports null).
+TC_DRAM_BYTES_PER_ITEM_B400 = (806.572544e6 + 149.506560e6) / 64
+# configurations 18 and 19 run the same launch at b = 400 (one K part under either policy)
+TC_PROFILED_CONFIGS = (18, 19)
 GOLDEN = os.path.join(ROOT, "tests", "golden", "c1_oracle.json")
 
 
@@ -490,7 +492,7 @@ def main():
         "gj_panel_share_of_step": pan_ms / ms if ms > 0 else None,
         "traffic": (TC_DRAM_BYTES_PER_ITEM_B400 * (alg / max(n_launch, 1)) / (8.0 * WORK["b"] ** 3)
                     if TC_DRAM_BYTES_PER_ITEM_B400 and WORK["b"] == 400 and n_launch
-                    and mixed and negf.tc_config() == TC_PROFILED_CONFIG
+                    and prec == negf.PREC_MIXED and negf.tc_config() in TC_PROFILED_CONFIGS
                     else None),
         "traffic_unit": "bytes per launch (DRAM read + write, ncu capture of 64 items scaled "
                         "to the launch's items)",
@@ -600,12 +602,44 @@ def extras(args, negf, torch, device, dvc, Hd, dev_np, E, wE, wk, prec):
         negf.rgf_solve(device, Et, st, lead["sigma_R"], lead["sigma_L"], o64)
         ev1.record()
         torch.cuda.synchronize()
-        v64 = fpn / (ev0.elapsed_time(ev1) / 1e3)
+        sec = ev0.elapsed_time(ev1) / 1e3
+        v64 = fpn / sec
+        # executed block work of the FP64 form (complex b^3 GEMM-equivalents, an inverse counted
+        # as one): decimation steps per side as run, then the sweeps of negf_rgf_solve
+        N, b = WORK["N"], WORK["b"]
+        iters = float(lead["iters"].sum().item())
+        eq = iters * 7 + fpn * (2 * 2 + 4) + fpn * (2 + 5 * (N - 2) + 7 + 2 + 6 * (N - 1) + N)
+        flops64 = eq * 8.0 * b ** 3
+        peak64 = fp64_peak(torch)
         out["fp64_gpu"] = {"value": v64, "unit": "points/s", "points": fpn,
                            "sample": f"{fpn} points of the workload in one batch (the FP64 "
                                      "form's rate saturates with the batch: 0.93 / 1.35 / 1.59 "
-                                     "points/s at 4 / 16 / 64 points)"}
+                                     "points/s at 4 / 16 / 64 points)",
+                           "roofline": {"bound": "fp64", "unit": "TFLOP/s",
+                                        "achieved": flops64 / sec / 1e12, "peak": peak64,
+                                        "frac": flops64 / sec / 1e12 / peak64,
+                                        "peak_kind": "cuBLAS DGEMM 8192^3 measured in this run",
+                                        "executed_flops_per_point": flops64 / fpn}}
     return out
+
+
+def fp64_peak(torch):
+    """FP64 dense rate of this GPU: cuBLAS DGEMM of 8192^3 through torch, best of 3."""
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    a @ b
+    torch.cuda.synchronize()
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2.0 * n ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    del a, b
+    return best
 
 
 def tier_bits(negf, prec):
