@@ -218,6 +218,18 @@ negf_status negf_scba_step(int32_t n_k, int32_t n_E, int32_t n_orb, const double
                            const double* diagGR, const double* diagGL, double* sigma_R,
                            double* sigma_L, double* delta_out, void* stream);
 
+/* The Born update of negf_scba_step on a non-uniform energy mesh E[n_E] (device double,
+ * strictly increasing; e.g. an adaptively refined mesh): the optical terms of Eqs. 5-6 take
+ * sum_k w_k dG(k, E_j +- hw) by linear interpolation between the two mesh points around
+ * E_j +- hw (hw in eV), and energies outside [E_0, E_{n_E - 1}] contribute zero.  On a uniform
+ * mesh with hw a whole number of steps it equals negf_scba_step (to rounding).  Other arguments
+ * and layouts as for negf_scba_step. */
+negf_status negf_scba_step_mesh(int32_t n_k, int32_t n_E, int32_t n_orb, const double* E,
+                                const double* w_k, double D_ac, double D_op, double hw,
+                                double n0, double mix, const double* diagGR,
+                                const double* diagGL, double* sigma_R, double* sigma_L,
+                                double* delta_out, void* stream);
+
 /* Reverse-mode derivative of the observables of negf_rgf_solve with respect to the on-site
  * potential V (the e Phi of Eq. 1), for a Newton-Poisson loop around Eq. 9.  With the
  * same inputs as negf_rgf_solve (self-energies held fixed) and the cotangents

@@ -318,6 +318,63 @@ def scba_step(dGR, dGL, wk, D_ac, D_op, shift, n0, sig_old_R, sig_old_L, mix=1.0
     return newR, newL, float(delta)
 
 
+def interp_on_mesh(values, E, x):
+    """Linear interpolation of values[j] (rows over the sorted mesh E) at energy x; zero when x
+    lies outside [E[0], E[-1]]."""
+    E = np.asarray(E, dtype=np.float64)
+    if x < E[0] or x > E[-1]:
+        return np.zeros_like(values[0])
+    m = int(np.searchsorted(E, x, side="right")) - 1
+    if m >= len(E) - 1:
+        return values[len(E) - 1].copy()
+    t = (x - E[m]) / (E[m + 1] - E[m])
+    return (1.0 - t) * values[m] + t * values[m + 1]
+
+
+def scba_selfenergy_mesh(dGR, dGL, wk, E, D_ac, D_op, hw, n0):
+    """Eqs. (4)-(6) on a non-uniform energy mesh E: as scba_selfenergy, with diag G at E +- hw
+    taken by linear interpolation between the mesh points around it (zero off the mesh)."""
+    dGR = np.asarray(dGR, dtype=np.complex128)
+    dGL = np.asarray(dGL, dtype=np.complex128)
+    n_k, n_E, n_orb = dGR.shape
+    sumR = np.zeros((n_E, n_orb), dtype=np.complex128)
+    sumL = np.zeros((n_E, n_orb), dtype=np.complex128)
+    for k in range(n_k):
+        sumR = sumR + wk[k] * dGR[k]
+        sumL = sumL + wk[k] * dGL[k]
+    sigR = np.zeros((n_E, n_orb), dtype=np.complex128)
+    sigL = np.zeros((n_E, n_orb), dtype=np.complex128)
+    for j in range(n_E):
+        up, dn = E[j] + hw, E[j] - hw
+        sigR[j] = D_ac * sumR[j] + D_op * ((1.0 + n0) * interp_on_mesh(sumR, E, dn)
+                                           + n0 * interp_on_mesh(sumR, E, up)
+                                           + 0.5 * interp_on_mesh(sumL, E, dn)
+                                           - 0.5 * interp_on_mesh(sumL, E, up))
+        sigL[j] = D_ac * sumL[j] + D_op * ((1.0 + n0) * interp_on_mesh(sumL, E, up)
+                                           + n0 * interp_on_mesh(sumL, E, dn))
+    return sigR, sigL
+
+
+def scba_step_mesh(dGR, dGL, wk, E, D_ac, D_op, hw, n0, sig_old_R, sig_old_L, mix=1.0):
+    """One Born update on a non-uniform mesh with linear mixing."""
+    nR, nL = scba_selfenergy_mesh(dGR, dGL, wk, E, D_ac, D_op, hw, n0)
+    newR = (1.0 - mix) * sig_old_R + mix * nR
+    newL = (1.0 - mix) * sig_old_L + mix * nL
+    delta = max(np.abs(newR - sig_old_R).max(), np.abs(newL - sig_old_L).max())
+    return newR, newL, float(delta)
+
+
+def trapezoid_weights(E):
+    """Trapezoid weights of a sorted, possibly non-uniform energy mesh."""
+    E = np.asarray(E, dtype=np.float64)
+    w = np.zeros(len(E))
+    for j in range(len(E) - 1):
+        h = E[j + 1] - E[j]
+        w[j] += 0.5 * h
+        w[j + 1] += 0.5 * h
+    return w
+
+
 # ----------------------------------------------------------------------------------------------
 # Gradient of the observables with respect to the on-site potential (dense definition)
 # ----------------------------------------------------------------------------------------------

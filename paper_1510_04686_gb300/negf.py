@@ -57,7 +57,7 @@ EXPORTS = ("negf_default_options", "negf_abi_version", "negf_status_string",
            "negf_launch_count", "negf_zinv_batched_noalloc", "negf_tc_config_count",
            "negf_tc_config_set", "negf_tc_config_get", "negf_last_cuda_error",
            "negf_fp64_fallback_count", "negf_debug_fail_waits", "negf_poisson_apply",
-           "negf_orbitals_to_atoms", "negf_atoms_to_orbitals")
+           "negf_orbitals_to_atoms", "negf_atoms_to_orbitals", "negf_scba_step_mesh")
 
 
 def library():
@@ -125,6 +125,9 @@ def library():
     lib.negf_tc_config_get.restype = c_int32
     lib.negf_last_cuda_error.argtypes = []
     lib.negf_last_cuda_error.restype = ctypes.c_char_p
+    lib.negf_scba_step_mesh.argtypes = [c_int32, c_int32, c_int32, P, P, c_double, c_double,
+                                        c_double, c_double, c_double, P, P, P, P, P, P]
+    lib.negf_scba_step_mesh.restype = c_int32
     lib.negf_poisson_apply.argtypes = [c_int32, c_int32, c_double, c_double, c_double, c_double,
                                        c_double, P, P, P, P, P]
     lib.negf_poisson_apply.restype = c_int32
@@ -289,6 +292,26 @@ def scba_step(diagGR, diagGL, w_k, sigma_R, sigma_L, D_ac, D_op, shift, n0, mix=
                                     int(shift), float(n0), float(mix), _ptr(diagGR),
                                     _ptr(diagGL), _ptr(sigma_R), _ptr(sigma_L), _ptr(delta),
                                     _stream()), "negf_scba_step")
+    return delta
+
+
+def scba_step_mesh(diagGR, diagGL, w_k, E, sigma_R, sigma_L, D_ac, D_op, hw, n0, mix=1.0):
+    """Born update on a non-uniform energy mesh E [n_E] (negf_scba_step_mesh): optical terms at
+    E +- hw by linear interpolation; sigma_R/L [n_E, n_orb] are updated in place.  Returns the
+    device scalar max|dSigma|."""
+    _need(diagGR, torch.complex128, "diagGR")
+    n_k, n_E, n_orb = diagGR.shape
+    _need(diagGL, torch.complex128, "diagGL", (n_k, n_E, n_orb))
+    _need(w_k, torch.float64, "w_k", (n_k,))
+    _need(E, torch.float64, "E", (n_E,))
+    _need(sigma_R, torch.complex128, "sigma_R", (n_E, n_orb))
+    _need(sigma_L, torch.complex128, "sigma_L", (n_E, n_orb))
+    delta = torch.empty((1,), dtype=torch.float64, device=diagGR.device)
+    _check(library().negf_scba_step_mesh(n_k, n_E, n_orb, _ptr(E), _ptr(w_k), float(D_ac),
+                                         float(D_op), float(hw), float(n0), float(mix),
+                                         _ptr(diagGR), _ptr(diagGL), _ptr(sigma_R),
+                                         _ptr(sigma_L), _ptr(delta), _stream()),
+           "negf_scba_step_mesh")
     return delta
 
 

@@ -541,3 +541,46 @@ def test_poisson_newton_converges_quadratically_to_the_picard_fixed_point():
         Up = 0.75 * Up + 0.25 * np.linalg.solve(K, rhs).reshape(N, A)
     assert np.abs(Up - U).max() < 1e-9
     assert np.abs(U).max() > 1e-3   # a non-trivial potential
+
+
+# ---- non-uniform energy meshes -----------------------------------------------------------------
+
+def test_scba_on_a_uniform_mesh_equals_the_index_shift_form():
+    """On a uniform mesh with hbar omega a whole number of steps the interpolated Born update is
+    the index-shifted one of Eqs. 4-6 (reading: E +- hbar omega, off-grid energies contribute 0)."""
+    rng = np.random.default_rng(21)
+    n_k, n_E, n_orb, sh = 2, 40, 5, 6
+    dGR = rng.normal(size=(n_k, n_E, n_orb)) + 1j * rng.normal(size=(n_k, n_E, n_orb))
+    dGL = 1j * rng.random((n_k, n_E, n_orb))
+    wk = np.array([0.3, 0.7])
+    dE = 0.0078125                      # a power of two: E_j + s dE lands on mesh points exactly
+    E = -0.25 + dE * np.arange(n_E)
+    a = O.scba_selfenergy(dGR, dGL, wk, 0.01, 0.02, sh, 0.11)
+    b = O.scba_selfenergy_mesh(dGR, dGL, wk, E, 0.01, 0.02, sh * dE, 0.11)
+    assert np.abs(a[0] - b[0]).max() < 1e-15 and np.abs(a[1] - b[1]).max() < 1e-15
+
+
+def test_scba_mesh_interpolation_is_exact_for_linear_diag_g():
+    """diag G linear in E on a random non-uniform mesh: the optical terms equal the line at
+    E +- hbar omega wherever that lies on the mesh, and vanish off it."""
+    rng = np.random.default_rng(22)
+    E = np.sort(rng.uniform(-1.0, 1.0, 30))
+    slope = rng.normal(size=3) + 1j * rng.normal(size=3)
+    icpt = rng.normal(size=3) + 1j * rng.normal(size=3)
+    line = lambda e: icpt + slope * e
+    dG = np.array([[line(e) for e in E]])          # one k-point, weight 1
+    hw = 0.137
+    sR, sL = O.scba_selfenergy_mesh(dG, dG, np.ones(1), E, 0.0, 1.0, hw, 0.25)
+    for j, e in enumerate(E):
+        up = line(e + hw) if e + hw <= E[-1] else 0.0
+        dn = line(e - hw) if e - hw >= E[0] else 0.0
+        assert np.allclose(sL[j], 1.25 * up + 0.25 * dn, atol=1e-13)
+        assert np.allclose(sR[j], 1.25 * dn + 0.25 * up + 0.5 * dn - 0.5 * up, atol=1e-13)
+
+
+def test_trapezoid_weights_integrate_lines_exactly_on_any_mesh():
+    rng = np.random.default_rng(23)
+    E = np.sort(rng.uniform(-2.0, 3.0, 17))
+    w = O.trapezoid_weights(E)
+    assert abs(w.sum() - (E[-1] - E[0])) < 1e-14
+    assert abs((w * (2.0 * E + 1.0)).sum() - ((E[-1] ** 2 + E[-1]) - (E[0] ** 2 + E[0]))) < 1e-13
