@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU-oracle, FP64-GPU and end-to-end side measurements")
     ap.add_argument("--workload", default="rgf",
-                    choices=["rgf", "scba", "adjoint", "ragged", "gemm"],
+                    choices=["rgf", "scba", "adjoint", "ragged", "gemm", "iface"],
                     help="rgf: the throughput line above; scba / adjoint / ragged / gemm: side "
                          "measurements of the Born loop (N=70, b=600), the adjoint sweep "
                          "(b=3430), ragged block sizes (b=200..800) and the batched tensor-core "
@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--tc-config", type=int, default=None,
                     help="tensor-core GEMM configuration (default: autotuned per block size "
                          "and batch for the rgf workload, the library default otherwise)")
+    ap.add_argument("--iface-orbitals", type=int, default=100,
+                    help="rows and columns of the hopping support in --workload iface")
     ap.add_argument("--gemm-b", type=int, default=400)
     ap.add_argument("--gemm-batch", type=int, default=64)
     return ap.parse_args()
@@ -302,6 +304,41 @@ def run_side(args):
                     dtype="bf16-slices->fp32 (fp64 storage)",
                     config={"workload": f"adjoint, N={N} slabs x 3430 orbitals (343 atoms x 10),"
                                         " V ~ U(-0.3, 0.3) eV per atom, 1 point"})
+    elif args.workload == "iface":
+        # the benchmark device with interface couplings: every hopping block keeps only the
+        # orbitals of the 10 facing atoms of each slab (its last 100 rows, first 100 columns)
+        from workloads import hamiltonian_k, k_grid, energy_grid_linspace
+        r = c = args.iface_orbitals
+        dv = make_device(WORK["N"], WORK["b"], WORK["seed"], ge_frac=WORK["ge_frac"],
+                         with_k=True, iface=(r, c))
+        ks, _ = k_grid(WORK["n_k"])
+        Hd = torch.as_tensor(np.stack([hamiltonian_k(dv, float(k))[0] for k in ks]), device=dvc)
+        Hu = torch.as_tensor(np.ascontiguousarray(np.broadcast_to(dv.T, (WORK["n_k"],) + dv.T.shape)),
+                             device=dvc)
+        E_all, _ = energy_grid_linspace(-3.0, 3.0, WORK["n_E"])
+        P = args.points_per_step
+        Et = torch.as_tensor(E_all[(np.arange(P) * 7) % WORK["n_E"]], device=dvc)
+        st = torch.as_tensor((np.arange(P) % WORK["n_k"]).astype(np.int32), device=dvc)
+        opt = negf.options(precision=negf.PREC_MIXED, chunk=P)
+        rates = {}
+        for name, iface in (("interface", (r, c)), ("dense", None)):
+            d = negf.Device(Hd, Hu, iface=iface)
+            lead = negf.lead_selfenergy(d, Et, st, opt)
+
+            def solve():
+                return negf.rgf_solve(d, Et, st, lead["sigma_R"], lead["sigma_L"], opt)
+            ms, out = _timed(torch, solve, args.warmup, args.steps)
+            rates[name] = (P * args.steps / (ms / 1e3), ms / args.steps, out)
+        dn = (rates["interface"][2]["density"] - rates["dense"][2]["density"]).abs().max().item()
+        line.update(metric="RGF sweeps energy-points/s with interface couplings (leads held)",
+                    unit="points/s", value=rates["interface"][0],
+                    ms_per_step=rates["interface"][1], dtype="bf16-slices->fp32 (fp64 storage)",
+                    config={"workload": f"N=70 slabs x 400x400 blocks, hoppings between the "
+                                        f"{r // 10} facing atoms of each slab ({r} x {c} support),"
+                                        f" {P} points",
+                            "dense_sweeps_points_per_s": rates["dense"][0],
+                            "speedup_vs_dense_sweeps": rates["interface"][0] / rates["dense"][0],
+                            "max_density_difference_vs_dense": dn})
     elif args.workload == "gemm":
         b, nb = args.gemm_b, args.gemm_batch
         if args.tc_config is not None:

@@ -100,10 +100,21 @@ typedef struct {
   int32_t n_sys;
   int32_t n_slabs;       /* N >= 1; N == 1 has no hopping and flat leads (Sigma_lead = 0) */
   int32_t block;         /* b >= 1 */
-  int32_t reserved;
+  int32_t iface_rows;    /* r in [0, b]: every H_{i,i+1} is nonzero only in its last r rows
+                            (the atoms of slab i facing slab i+1); 0 = all b rows            */
   const double* H_diag;  /* device, complex128 [n_sys][N][b][b] */
   const double* H_up;    /* device, complex128 [n_sys][N-1][b][b]; may be NULL when N == 1 */
+  int32_t iface_cols;    /* c in [0, b]: ... and only in its first c columns (the atoms of
+                            slab i+1 facing slab i); 0 = all b columns                       */
+  int32_t reserved;
 } negf_device;
+/* Interface couplings (iface_rows / iface_cols below b): real tight-binding hoppings connect
+ * only the atoms at the facing surfaces of neighbouring slabs, so H_{i,i+1} = E_R T E_C^T with
+ * T the r x c block of its last r rows and first c columns.  negf_rgf_solve then forms every
+ * product with a hopping on that support only (the Sigma_eff term t^H g t costs 2 r c (b or c)
+ * instead of 2 b^3, and each backward product contracts over r or c instead of b); entries of
+ * H_up outside the support must be zero (the lead decimation and the adjoint use the full
+ * blocks, and so does the dense path). */
 
 typedef struct {
   double eta_lead;       /* imaginary part of z = E + i eta in the lead decimation (eV)   */

@@ -253,7 +253,7 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
         Y = Fc(T[0]);
       }
       CK(launch_assemble(s, P, b, a.E, eta, Hd(i), a.V ? a.V + (size_t)i * b : nullptr,
-                         a.scatR ? a.scatR + (size_t)i * b : nullptr, NB, erow, Y,
+                         a.scatR ? a.scatR + (size_t)i * b : nullptr, NB, erow, Y, b,
                          i == 0 ? SigL_R : none, i == N - 1 ? SigR_R : none, F(T[1]), nullptr));
       CK(eng.inv(P, F(T[1]), F(gF(i)), a.status, nullptr));
       bool prev = false;

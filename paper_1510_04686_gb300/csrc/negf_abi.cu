@@ -39,6 +39,9 @@ constexpr size_t kDefaultBudget = 24ull << 30;
 bool valid_dev(const negf_device* d) {
   if (!d || d->n_sys < 1 || d->n_slabs < 1 || d->block < 1 || !d->H_diag) return false;
   if (d->n_slabs > 1 && !d->H_up) return false;
+  if (d->iface_rows < 0 || d->iface_rows > d->block || d->iface_cols < 0 ||
+      d->iface_cols > d->block)
+    return false;
   return true;
 }
 
@@ -292,32 +295,52 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
   auto F = [&](z64* p) { return flat(p, bb, b); };
   auto Fc = [&](z64* p) { return cst(flat(p, bb, b)); };
   auto Lb = [&](int i) { return w.Lb + (size_t)i * P * bb; };
+  // Interface couplings: H_{i,i+1} is nonzero only in its last ir rows and first ic columns
+  // (ir = ic = b: dense).  Views of the b x b blocks (same batch stride and leading dimension):
+  // columns from c0, rows from r0, and the ir x ic support of a hopping block.
+  const int ir = dev->iface_rows > 0 ? dev->iface_rows : b;
+  const int ic = dev->iface_cols > 0 ? dev->iface_cols : b;
+  auto cview = [](BMc<double> X, int c0) {
+    X.p += c0;
+    return X;
+  };
+  auto rview = [](BMc<double> X, int r0) {
+    X.p += (long long)r0 * X.ld;
+    return X;
+  };
+  auto bcview = [](BM<double> X, int c0) {
+    X.p += c0;
+    return X;
+  };
+  auto tview = [&](BMc<double> X) { return rview(X, b - ir); };
 
   // ---- forward sweep: left-connected g_i, g^<_i
   for (int i = 0; i < N; ++i) {
     const bool first = (i == 0), last = (i == N - 1);
     BMc<double> Y = kNone;
     if (!first) {
-      // L_{i-1} = g_{i-1} t_{i-1} (kept for the backward sweep);  Y = t^H L
-      CK(eng.gemm(P, b, b, b, one, Fc(G[i - 1]), OP_N, Hu(i - 1), OP_N, zero, F(Lb(i - 1)), zero,
-                  kNone, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Hu(i - 1), OP_C, Fc(Lb(i - 1)), OP_N, zero, F(w.Y), zero,
-                  kNone, nullptr));
+      // L_{i-1} = g_{i-1} t_{i-1} (kept for the backward sweep);  Y = t^H L.  Interface mode:
+      // t = E_R T E_C^T, so only L[:, C] = g[:, R] T and Y[C, C] = T^H L[R, C] are formed.
+      CK(eng.gemm(P, b, ic, ir, one, cview(Fc(G[i - 1]), b - ir), OP_N, tview(Hu(i - 1)), OP_N,
+                  zero, F(Lb(i - 1)), zero, kNone, nullptr));
+      CK(eng.gemm(P, ic, ic, ir, one, tview(Hu(i - 1)), OP_C, rview(Fc(Lb(i - 1)), b - ir), OP_N,
+                  zero, F(w.Y), zero, kNone, nullptr));
       Y = Fc(w.Y);
     }
     CK(launch_assemble(s, P, b, a.E, eta, Hd(i), a.V ? a.V + (size_t)i * b : nullptr,
-                       a.scatR ? a.scatR + (size_t)i * b : nullptr, NB, erow, Y,
+                       a.scatR ? a.scatR + (size_t)i * b : nullptr, NB, erow, Y, ic,
                        first ? SigL_R : kNone, last ? SigR_R : kNone, F(w.Mt), nullptr));
     CK(eng.inv(P, F(w.Mt), F(G[i]), a.status, nullptr));
     bool have_prev = false;
     if (!first) {
-      // g^<_i = K g^<_{i-1} K^H with K = g_i t_{i-1}^H
-      CK(eng.gemm(P, b, b, b, one, Fc(G[i]), OP_N, Hu(i - 1), OP_C, zero, F(w.K), zero, kNone,
-                  nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(GL[i - 1]), OP_N, Fc(w.K), OP_C, zero, F(w.Vt), zero,
-                  kNone, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(w.K), OP_N, Fc(w.Vt), OP_N, zero, F(GL[i]), zero, kNone,
-                  nullptr));
+      // g^<_i = K g^<_{i-1} K^H with K = g_i t_{i-1}^H; interface mode: only K[:, R] =
+      // g_i[:, C] T^H, then Vt = g^<_{i-1}[:, R] K[:, R]^H and g^<_i = K[:, R] Vt[R, :]
+      CK(eng.gemm(P, b, ir, ic, one, Fc(G[i]), OP_N, tview(Hu(i - 1)), OP_C, zero,
+                  bcview(F(w.K), b - ir), zero, kNone, nullptr));
+      CK(eng.gemm(P, b, b, ir, one, cview(Fc(GL[i - 1]), b - ir), OP_N, cview(Fc(w.K), b - ir),
+                  OP_C, zero, F(w.Vt), zero, kNone, nullptr));
+      CK(eng.gemm(P, b, b, ir, one, cview(Fc(w.K), b - ir), OP_N, rview(Fc(w.Vt), b - ir), OP_N,
+                  zero, F(GL[i]), zero, kNone, nullptr));
       have_prev = true;
     }
     const bool has_src = first || last || a.scatL != nullptr;
@@ -351,22 +374,25 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
   z64* spare = w.Gn;
   for (int i = N - 2; i >= 0; --i) {
     z64* L = Lb(i);
-    // W = G_{i+1} t_i^H;  LW = L W;  G_i = g_i + LW g_i
-    CK(eng.gemm(P, b, b, b, one, Fc(G[i + 1]), OP_N, Hu(i), OP_C, zero, F(w.W), zero, kNone,
+    // W = G_{i+1} t_i^H;  LW = L W;  G_i = g_i + LW g_i.  Interface mode (L has columns C,
+    // t_i^H rows C and columns R): W[:, R] = G_{i+1}[:, C] T^H, LW[:, R] = L[:, C] W[C, R],
+    // G_i = g_i + LW[:, R] g_i[R, :]
+    CK(eng.gemm(P, b, ir, ic, one, Fc(G[i + 1]), OP_N, tview(Hu(i)), OP_C, zero,
+                bcview(F(w.W), b - ir), zero, kNone, nullptr));
+    CK(eng.gemm(P, b, ir, ic, one, Fc(L), OP_N, cview(Fc(w.W), b - ir), OP_N, zero,
+                bcview(F(w.LW), b - ir), zero, kNone, nullptr));
+    CK(eng.gemm(P, b, b, ir, one, cview(Fc(w.LW), b - ir), OP_N, rview(Fc(G[i]), b - ir), OP_N,
+                zero, F(spare), one, Fc(G[i]), nullptr));
+    // Q = G^<_{i+1} L^H;  U = 2 W g^<_i + Q;  G^<_{i+1,i} = (U + Q) / 2  (interface mode:
+    // Q = G^<_{i+1}[:, C] L[:, C]^H, U = 2 W[:, R] g^<_i[R, :] + Q)
+    CK(eng.gemm(P, b, b, ic, one, Fc(GL[i + 1]), OP_N, Fc(L), OP_C, zero, F(w.Qm), zero, kNone,
                 nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(L), OP_N, Fc(w.W), OP_N, zero, F(w.LW), zero, kNone,
-                nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(w.LW), OP_N, Fc(G[i]), OP_N, zero, F(spare), one, Fc(G[i]),
-                nullptr));
-    // Q = G^<_{i+1} L^H;  U = 2 W g^<_i + Q;  G^<_{i+1,i} = (U + Q) / 2
-    CK(eng.gemm(P, b, b, b, one, Fc(GL[i + 1]), OP_N, Fc(L), OP_C, zero, F(w.Qm), zero, kNone,
-                nullptr));
-    CK(eng.gemm(P, b, b, b, two, Fc(w.W), OP_N, Fc(GL[i]), OP_N, zero, F(w.U), one, Fc(w.Qm),
-                nullptr));
+    CK(eng.gemm(P, b, b, ir, two, cview(Fc(w.W), b - ir), OP_N, rview(Fc(GL[i]), b - ir), OP_N,
+                zero, F(w.U), one, Fc(w.Qm), nullptr));
     if (a.current)
       CK(launch_bond_current(s, P, b, Hu(i), Fc(w.U), Fc(w.Qm), a.current + i, N - 1, nullptr));
-    // G^<_ii = AH(g^<_i + L U)
-    CK(eng.gemm(P, b, b, b, one, Fc(L), OP_N, Fc(w.U), OP_N, zero, F(w.Mt), one, Fc(GL[i]),
+    // G^<_ii = AH(g^<_i + L U)  (interface mode: L[:, C] U[C, :])
+    CK(eng.gemm(P, b, b, ic, one, Fc(L), OP_N, Fc(w.U), OP_N, zero, F(w.Mt), one, Fc(GL[i]),
                 nullptr));
     CK(launch_antiherm(s, P, b, Fc(w.Mt), F(GL[i]), nullptr));
     std::swap(G[i], spare);

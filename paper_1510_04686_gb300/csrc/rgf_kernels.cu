@@ -38,8 +38,8 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 
 __global__ void k_assemble(int b, const double* E, double eta, BMc<double> Hd, const double* V,
                            const z64* scat, long long scat_stride, const int32_t* e_idx,
-                           BMc<double> Y, BMc<double> SigA, BMc<double> SigB, BM<double> M,
-                           const int32_t* active) {
+                           BMc<double> Y, int ny, BMc<double> SigA, BMc<double> SigB,
+                           BM<double> M, const int32_t* active) {
   const int p = blockIdx.y;
   if (active && !active[p]) return;
   const z64* h = bat(Hd, p);
@@ -58,7 +58,7 @@ __global__ void k_assemble(int b, const double* E, double eta, BMc<double> Hd, c
       v.im += eta;
       if (sc) v = v - sc[r];
     }
-    if (y) v = v - y[(long long)r * Y.ld + c];
+    if (y && r < ny && c < ny) v = v - y[(long long)r * Y.ld + c];
     if (sa) v = v - sa[(long long)r * SigA.ld + c];
     if (sb) v = v - sb[(long long)r * SigB.ld + c];
     m[(long long)r * M.ld + c] = v;
@@ -347,10 +347,10 @@ inline dim3 grid2(long long work, int P) {
 cudaError_t launch_assemble(cudaStream_t s, int P, int b, const double* E, double eta,
                             BMc<double> Hd, const double* V, const z64* scat,
                             long long scat_stride, const int32_t* e_idx, BMc<double> Y,
-                            BMc<double> SigA, BMc<double> SigB, BM<double> M,
+                            int ny, BMc<double> SigA, BMc<double> SigB, BM<double> M,
                             const int32_t* active) {
   k_assemble<<<grid2((long long)b * b, P), kT, 0, s>>>(b, E, eta, Hd, V, scat, scat_stride,
-                                                       e_idx, Y, SigA, SigB, M, active);
+                                                       e_idx, Y, ny, SigA, SigB, M, active);
   count_launch();
   return cudaGetLastError();
 }

@@ -7,7 +7,7 @@ namespace negf {
 cudaError_t launch_assemble(cudaStream_t s, int P, int b, const double* E, double eta,
                             BMc<double> Hd, const double* V, const z64* scat,
                             long long scat_stride, const int32_t* e_idx, BMc<double> Y,
-                            BMc<double> SigA, BMc<double> SigB, BM<double> M,
+                            int ny, BMc<double> SigA, BMc<double> SigB, BM<double> M,
                             const int32_t* active);
 cudaError_t launch_source(cudaStream_t s, int P, int b, const z64* scat, long long scat_stride,
                           const int32_t* e_idx, BMc<double> SigA, BMc<double> SigB,

@@ -37,7 +37,8 @@ class NegfError(RuntimeError):
 
 class _Dev(ctypes.Structure):
     _fields_ = [("n_sys", c_int32), ("n_slabs", c_int32), ("block", c_int32),
-                ("reserved", c_int32), ("H_diag", c_void_p), ("H_up", c_void_p)]
+                ("iface_rows", c_int32), ("H_diag", c_void_p), ("H_up", c_void_p),
+                ("iface_cols", c_int32), ("reserved", c_int32)]
 
 
 class _Opt(ctypes.Structure):
@@ -179,9 +180,12 @@ def _stream():
 
 
 class Device:
-    """Block-tridiagonal Hamiltonians H_diag [n_sys,N,b,b], H_up [n_sys,N-1,b,b] (complex128)."""
+    """Block-tridiagonal Hamiltonians H_diag [n_sys,N,b,b], H_up [n_sys,N-1,b,b] (complex128).
 
-    def __init__(self, H_diag: torch.Tensor, H_up: torch.Tensor | None):
+    iface=(r, c): every H_{i,i+1} is nonzero only in its last r rows and first c columns (the
+    facing atoms of neighbouring slabs); the sweeps then contract over r or c instead of b."""
+
+    def __init__(self, H_diag: torch.Tensor, H_up: torch.Tensor | None, iface=None):
         _need(H_diag, torch.complex128, "H_diag")
         if H_diag.dim() != 4 or H_diag.shape[2] != H_diag.shape[3]:
             raise ValueError("H_diag must be [n_sys, N, b, b]")
@@ -190,8 +194,10 @@ class Device:
             _need(H_up, torch.complex128, "H_up", (n_sys, N - 1, b, b))
         self.H_diag, self.H_up = H_diag, H_up
         self.n_sys, self.N, self.b = int(n_sys), int(N), int(b)
-        self.c = _Dev(self.n_sys, self.N, self.b, 0, H_diag.data_ptr(),
-                      H_up.data_ptr() if (H_up is not None and N > 1) else None)
+        r, c = (0, 0) if iface is None else (int(iface[0]), int(iface[1]))
+        self.iface = iface
+        self.c = _Dev(self.n_sys, self.N, self.b, r, H_diag.data_ptr(),
+                      H_up.data_ptr() if (H_up is not None and N > 1) else None, c, 0)
 
 
 _WS = {}

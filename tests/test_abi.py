@@ -111,7 +111,7 @@ def test_binding_refuses_cpu_tensors():
 def test_options_struct_layout():
     # six doubles and eight 32-bit integers, as in include/negf.h
     assert ctypes.sizeof(B._Opt) == 6 * 8 + 8 * 4
-    assert ctypes.sizeof(B._Dev) == 4 * 4 + 2 * 8
+    assert ctypes.sizeof(B._Dev) == 4 * 4 + 2 * 8 + 2 * 4
     o = negf.options()
     assert o.sr_host_check == 4
 
@@ -218,3 +218,13 @@ def test_precision_tiers_and_their_exact_ranges(lib):
                 dict(refine_max=-1)):
         o = negf.options(precision=B.PREC_MIXED, **bad)
         assert lib.negf_workspace_size(ctypes.byref(d), 8, ctypes.byref(o), B.WS_LEAD) == 0
+
+
+def test_interface_support_is_validated(lib):
+    """The interface-coupling support (last r rows, first c columns of every hopping block) must
+    lie in [0, b]."""
+    o = negf.options()
+    for r, c, ok in ((0, 0, True), (2, 3, True), (8, 8, True), (9, 0, False), (0, -1, False)):
+        d = B._Dev(1, 4, 8, r, 1, 1, c, 0)
+        size = lib.negf_workspace_size(ctypes.byref(d), 4, ctypes.byref(o), B.WS_RGF)
+        assert (size > 0) == ok, (r, c)

@@ -1,0 +1,57 @@
+"""Interface couplings (hoppings nonzero only between the facing atoms of neighbouring slabs):
+the sweeps restricted to the r x c support give the dense sweeps' results and the oracle's."""
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import make_device
+
+torch = pytest.importorskip("torch")
+negf = pytest.importorskip("paper_1510_04686_gb300")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    negf._build.build()
+    negf.library()
+
+
+def _t(x):
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda")
+
+
+def _solve(dev, E, opt, iface, V=None):
+    d = negf.Device(_t(dev.D[None]), _t(dev.T[None]), iface=iface)
+    Et = _t(E)
+    st = torch.zeros(len(E), dtype=torch.int32, device="cuda")
+    lead = negf.lead_selfenergy(d, Et, st, opt)
+    out = negf.rgf_solve(d, Et, st, lead["sigma_R"], lead["sigma_L"], opt,
+                         V=None if V is None else _t(V))
+    torch.cuda.synchronize()
+    return {k: v.cpu().numpy() for k, v in out.items() if isinstance(v, torch.Tensor)}
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("N,b,r,c", [(6, 60, 20, 30), (4, 140, 40, 40), (3, 50, 50, 10)])
+def test_interface_sweeps_match_dense_and_oracle(prec, N, b, r, c):
+    dev = make_device(N, b, 900 + b + r, ge_frac=0.1, iface=(r, c))
+    E = np.linspace(-1.6, 1.3, 6)
+    V = np.random.default_rng(b).uniform(-0.1, 0.1, (N, b))
+    opt = negf.options(precision=prec)
+    sparse = _solve(dev, E, opt, (r, c), V)
+    dense = _solve(dev, E, opt, None, V)
+    refs = [O.solve_point(dev.D, dev.T, e, 1e-6, V) for e in E]
+    tol = 1e-9 if prec == 0 else 1e-6
+    scale = max(np.abs(x["density"]).max() for x in refs)
+    jscale = max(np.abs(x["current"]).max() for x in refs)
+    for p, x in enumerate(refs):
+        for out in (sparse, dense):
+            assert np.abs(out["density"][p] - x["density"]).max() <= tol * scale
+            assert np.abs(out["current"][p] - x["current"]).max() <= tol * jscale
+            assert abs(out["transmission"][p] - x["transmission"]) <= \
+                tol * max(1.0, abs(x["transmission"]))
+    assert np.all(sparse["status"] == 0)
+    if prec == 0:  # same arithmetic on the nonzero blocks: rounding-level agreement
+        assert np.abs(sparse["density"] - dense["density"]).max() <= 1e-12 * scale

@@ -48,8 +48,12 @@ def _complex_normal(rng, shape, std):
 def make_device(N: int, b: int, seed: int, *, sigma_on: float = 0.3, diag_lo: float = -2.0,
                 diag_hi: float = 2.0, ge_frac: float = 0.0, ge_shift: float = 0.2,
                 with_k: bool = False, w_scale: float = 0.1,
-                hop_std: Optional[float] = None) -> Device:
-    """Draw one seeded device (all blocks complex128)."""
+                hop_std: Optional[float] = None, iface: Optional[tuple] = None) -> Device:
+    """Draw one seeded device (all blocks complex128).
+
+    iface=(r, c): interface couplings -- every hopping block H_{i,i+1} keeps only its last r
+    rows and first c columns (the orbitals of the atoms facing the neighbouring slab), the rest
+    is zero; the random draws are the same as without it."""
     if N < 1 or b < 1:
         raise ValueError("N and b must be positive")
     rng = np.random.default_rng(seed)
@@ -75,8 +79,14 @@ def make_device(N: int, b: int, seed: int, *, sigma_on: float = 0.3, diag_lo: fl
                 D[i, idx, idx] += ge_shift
     T = _complex_normal(rng, (max(N - 1, 0), b, b), hop)
     W = _complex_normal(rng, (N, b, b), w_scale / np.sqrt(b)) if with_k else None
+    if iface is not None:
+        r, c = iface
+        mask = np.zeros((b, b), dtype=bool)
+        mask[b - r:, :c] = True
+        T = np.where(mask[None], T, 0.0)
     return Device(N=N, b=b, D=D, T=T, W=W, ge_mask=ge_mask,
-                  meta=dict(seed=seed, sigma_on=sigma_on, ge_frac=ge_frac, with_k=with_k))
+                  meta=dict(seed=seed, sigma_on=sigma_on, ge_frac=ge_frac, with_k=with_k,
+                            iface=iface))
 
 
 def hamiltonian_k(dev: Device, k: float):
