@@ -355,11 +355,13 @@ negf_status negf_zinv_batched_noalloc(int32_t n_batch, int32_t n, double* M, dou
  * speed: configuration c uses the kernel shape c / 2 of
  *   (6 stages, 1 CTA, 1), (6, 1, 2), (6, 1, 3), (8 stages, CTA pair, 1), (8, 2, 2), (8, 2, 4),
  *   (3, 1, 1, 2 K chunks per stage), (4, 2, 1, 2 K chunks per stage),
- *   (2, 1, 1, 3 K chunks per stage), (2, 2, 1, 4 K chunks per stage)
+ *   (2, 1, 1, 3 K chunks per stage), (2, 2, 1, 4 K chunks per stage),
+ *   (3, 2, 1, 3 K chunks per stage), (2, 2, 1, 2 K chunks, 64-column tiles, 2 CTAs per SM),
+ *   (2, 1, 1, 2 K chunks, 64-column tiles, 2 CTAs per SM)
  * = (shared-memory pipeline stages, CTAs per MMA: one 128-row tile or a pair of CTAs with a
- * 256-row MMA, stages released per MMA commit; K chunks of 64 per stage) and splits K into at
- * most (4, 8)[c % 2] exactly accumulated parts (more parts allow wider slices and fewer slice
- * products for long contractions).
+ * 256-row MMA, stages released per MMA commit; K chunks of 64 per stage; 128-column tiles unless
+ * stated) and splits K into at most (4, 8)[c % 2] exactly accumulated parts (more parts allow
+ * wider slices and fewer slice products for long contractions).
  * negf_tc_config_set selects one process-wide (default 18: the CTA pair with 2 stages of 4 K
  * chunks); results agree to the GEMM's rounding.  The package's autotuner times them per block
  * size and stores the choice. */

@@ -152,6 +152,39 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
       "r"(r[29]), "r"(r[30]), "r"(r[31])
       : "memory");
 }
+// 16 consecutive TMEM columns of this warp's lane quarter
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32"
+      " {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32"
+      " [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+template <int W>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* r) {
+  if constexpr (W == 32)
+    tmem_ld32(taddr, r);
+  else
+    tmem_ld16(taddr, r);
+}
+template <int W>
+__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t* r) {
+  if constexpr (W == 32)
+    tmem_st32(taddr, r);
+  else
+    tmem_st16(taddr, r);
+}
 __device__ __forceinline__ void tmem_st_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -200,7 +233,10 @@ struct Cfg {
   static constexpr int kStage = kATile + kBTile;
   static constexpr int kStagingPerWarp = 32 * 8 * 16;         // 32 rows x 8 complex outputs
   static constexpr int kStaging = kEpiWarps * kStagingPerWarp;
-  static constexpr int kSmem = kStages * kStage + kStaging + 1024 + 256;  // + align + barriers
+  // the output staging of the tile's final pass reuses the pipeline stages (every MMA and load
+  // of the tile has completed by then)
+  static_assert(kStaging <= kStages * kStage, "staging fits the stage memory");
+  static constexpr int kSmem = kStages * kStage + 1024 + 256;  // + align + barriers
 };
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -249,8 +285,8 @@ __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
 
 // KPS: K chunks (of 64 BF16 columns) per shared-memory stage; more chunks per stage put more
 // MMAs behind each barrier wait and commit of the MMA thread.
-template <int NT, int STAGES, int CG, int G, int KPS = 1>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int NT, int STAGES, int CG, int G, int KPS = 1, int MINB = 1>
+__global__ void __launch_bounds__(kThreads, MINB)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const Sched sched, int M, int N2, int S, int two_beta,
               const int32_t* __restrict__ eA, const int32_t* __restrict__ fB,
@@ -259,7 +295,13 @@ __global__ void __launch_bounds__(kThreads, 1)
               z64 beta, z64 gamma, BM<double> C, BMc<double> D, int add_identity,
               int trunc_beta, const int32_t* active, int32_t* err, float* rmax, int Kc,
               int count_flops) {
-  static_assert(NT * (kAccBufs + 2) == 512, "TMEM: kAccBufs accumulators + hi / lo sum words");
+  // TMEM: kAccBufs accumulators + hi / lo sum words, a power of two of columns; two resident
+  // CTAs per SM (MINB = 2) must fit the SM's 512 columns together
+  constexpr uint32_t kTmemCols = NT * (kAccBufs + 2);
+  static_assert(kTmemCols * MINB <= 512 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM budget");
+  // epilogue columns per TMEM load: 16 in the register-lean two-CTA form
+  constexpr int CW = MINB == 1 ? 32 : 16;
+  static_assert((NT / 2) % CW == 0, "epilogue chunks");
   static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair per MMA");
   using CF = Cfg<NT, STAGES, CG, G, KPS>;
   constexpr int kStages = CF::kStages;
@@ -269,8 +311,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  z64* staging = reinterpret_cast<z64*>(smem + kStages * CF::kStage);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * CF::kStage + CF::kStaging);
+  z64* staging = reinterpret_cast<z64*>(smem);  // the final pass only (see Cfg)
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * CF::kStage);
   uint64_t* empty = full + kStages;  // one per group of G stages
   uint64_t* accfull = empty + CF::kGroups;
   uint64_t* accempty = accfull + kAccBufs;
@@ -335,13 +377,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if (warp == 9) {
     if constexpr (CG == 2) {
-      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                       smem_u32(tmem_slot))
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)), "r"(kTmemCols)
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     } else {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                       smem_u32(tmem_slot))
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)), "r"(kTmemCols)
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -514,23 +556,23 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!mbar_wait(&accfull[buf], (acc / kAccBufs) & 1, abort_flag)) break;
       tc_fence_after();
       const bool last = (acc == n_exec - 1);
-      for (int c0 = cbase; c0 < cbase + NT / 2; c0 += 32) {
-        uint32_t v[32], h[32], l[32];
-        tmem_ld32(tmem + lane_off + (uint32_t)(buf * NT + c0), v);
+      for (int c0 = cbase; c0 < cbase + NT / 2; c0 += CW) {
+        uint32_t v[CW], h[CW], l[CW];
+        tmem_ld<CW>(tmem + lane_off + (uint32_t)(buf * NT + c0), v);
         if (acc > 0) {
-          tmem_ld32(t_hi + c0, h);
-          tmem_ld32(t_lo + c0, l);
+          tmem_ld<CW>(t_hi + c0, h);
+          tmem_ld<CW>(t_lo + c0, l);
         }
         tmem_ld_wait();
         if (acc == 0) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < CW; ++j) {
             h[j] = v[j];
             l[j] = 0u;
           }
         } else {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < CW; ++j) {
             const float hj = __uint_as_float(h[j]), vj = __uint_as_float(v[j]);
             const float s1 = hj + vj;
             const float bp = s1 - hj;
@@ -542,14 +584,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
         if (!last) {
-          tmem_st32(t_hi + c0, h);
-          tmem_st32(t_lo + c0, l);
+          tmem_st<CW>(t_hi + c0, h);
+          tmem_st<CW>(t_lo + c0, l);
         } else {
           // Final value of this row's 16 complex outputs, written through a per-warp staging
           // tile so that C, D and the stores are accessed as contiguous 128-byte row segments.
           z64* stg = staging + warp * (32 * 8);
 #pragma unroll
-          for (int half8 = 0; half8 < 2; ++half8) {
+          for (int half8 = 0; half8 < CW / 16; ++half8) {
 #pragma unroll
             for (int jj = 0; jj < 8; ++jj) {
               const int j = 16 * half8 + 2 * jj;
@@ -612,10 +654,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 9) {
     tc_fence_after();
     if constexpr (CG == 2)
-      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(kTmemCols)
                    : "memory");
     else
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(kTmemCols)
                    : "memory");
   }
   if (threadIdx.x == 0 && *abort_flag && err) atomicExch(err, 1);
@@ -672,7 +716,7 @@ Sched build_sched(const TcPlan& pl, int n_chunks) {
   return sc;
 }
 
-template <int NT, int STAGES, int CG, int G, int KPS = 1>
+template <int NT, int STAGES, int CG, int G, int KPS = 1, int MINB = 1>
 cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int S, int two_beta,
                       const Sched& sc, const CUtensorMap& mA, const CUtensorMap& mB, const TcWs& ws,
                       const int32_t* zA, int zmA, const int32_t* zB, int zmB, z64 alpha,
@@ -682,7 +726,7 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int S, int tw
   static std::atomic<unsigned> attr{0};
   {
     cudaError_t e = set_smem_once(
-        attr, reinterpret_cast<const void*>(&k_tc_gemm<NT, STAGES, CG, G, KPS>), CF::kSmem);
+        attr, reinterpret_cast<const void*>(&k_tc_gemm<NT, STAGES, CG, G, KPS, MINB>), CF::kSmem);
     if (e != cudaSuccess) return e;
   }
   const int mt = (M + kBM - 1) / kBM;
@@ -703,7 +747,8 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int S, int tw
   at[0].val.clusterDim.z = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&lc, k_tc_gemm<NT, STAGES, CG, G, KPS>, mA, mB, sc, M, N2, S,
+  cudaError_t e = cudaLaunchKernelEx(&lc, k_tc_gemm<NT, STAGES, CG, G, KPS, MINB>, mA, mB, sc,
+                                     M, N2, S,
                                      two_beta, (const int32_t*)ws.expA, (const int32_t*)ws.expB,
                                      zA, zmA, zB, zmB, alpha, beta, gamma, C, D,
                                      add_identity ? 1 : 0, trunc_beta, active, ws.err, rmax,
@@ -721,12 +766,16 @@ cudaError_t launch_tc(cudaStream_t s, int P, int M, int N2, int K, int S, int tw
 // Every tcgen05.commit stalls the tensor pipe for a few hundred cycles, so releasing shared-
 // memory stages in groups (one commit per G stages) keeps the MMAs back to back.
 struct TcShape {
-  int stages, cg, grp;
+  int stages, cg, grp, nt;  // nt: real output columns per tile
 };
-constexpr TcShape kShapes[] = {{6, 1, 1}, {6, 1, 2}, {6, 1, 3}, {8, 2, 1}, {8, 2, 2}, {8, 2, 4},
-                               {3, 1, 1}, {4, 2, 1}, {2, 1, 1}, {2, 2, 1}};
-// shapes 6-9: several K chunks per stage: 2 (3 stages of 64 KB; a CTA pair: 4 stages of
-// 48 KB), 3 (2 stages of 96 KB), 4 (a CTA pair: 2 stages of 96 KB)
+constexpr TcShape kShapes[] = {{6, 1, 1, 128}, {6, 1, 2, 128}, {6, 1, 3, 128}, {8, 2, 1, 128},
+                               {8, 2, 2, 128}, {8, 2, 4, 128}, {3, 1, 1, 128}, {4, 2, 1, 128},
+                               {2, 1, 1, 128}, {2, 2, 1, 128}, {3, 2, 1, 128}, {2, 2, 1, 64},
+                               {2, 1, 1, 64}};
+// shapes 6-10: several K chunks per stage: 2 (3 stages of 64 KB; a CTA pair: 4 stages of
+// 48 KB), 3 (2 stages of 96 KB; a CTA pair: 3 stages of 72 KB), 4 (a CTA pair: 2 stages of
+// 96 KB).  Shapes 11-12: 64-column tiles (256 TMEM columns) with 2 stages of 2 K chunks, two
+// CTAs resident per SM so that one tile's waits and final pass overlap the other's MMAs.
 constexpr int kNumCfg = 2 * (int)(sizeof(kShapes) / sizeof(kShapes[0]));
 std::atomic<int> g_cfg{18};
 
@@ -891,7 +940,8 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
   if (e != cudaSuccess) return e;
   CUtensorMap mA, mB;
   if (!make_map(&mA, sa, L, M, (long long)PA * S, kBM)) return cudaErrorInvalidValue;
-  if (!make_map(&mB, sb, L, N2, (long long)PB * S, kNT / CG)) return cudaErrorInvalidValue;
+  const int NTc = kShapes[cfg / 2].nt;
+  if (!make_map(&mB, sb, L, N2, (long long)PB * S, NTc / CG)) return cudaErrorInvalidValue;
   if ((long long)pl.parts * S * (S + 1) / 2 > kMaxItems) return cudaErrorInvalidValue;
   const Sched sc = build_sched(pl, L / kKC);
 #define NEGF_TC_ARGS                                                                          \
@@ -908,6 +958,9 @@ cudaError_t tc_gemm(cudaStream_t s, int P, int M, int N, int K, z64 alpha, BMc<d
     case 7: return launch_tc<kNT, 4, 2, 1, 2>(NEGF_TC_ARGS);
     case 8: return launch_tc<kNT, 2, 1, 1, 3>(NEGF_TC_ARGS);
     case 9: return launch_tc<kNT, 2, 2, 1, 4>(NEGF_TC_ARGS);
+    case 10: return launch_tc<kNT, 3, 2, 1, 3>(NEGF_TC_ARGS);
+    case 11: return launch_tc<64, 2, 2, 1, 2, 2>(NEGF_TC_ARGS);
+    case 12: return launch_tc<64, 2, 1, 1, 2, 2>(NEGF_TC_ARGS);
     default: return launch_tc<kNT, 6, 1, 1>(NEGF_TC_ARGS);
   }
 #undef NEGF_TC_ARGS
