@@ -112,9 +112,12 @@ typedef struct {
  * only the atoms at the facing surfaces of neighbouring slabs, so H_{i,i+1} = E_R T E_C^T with
  * T the r x c block of its last r rows and first c columns.  negf_rgf_solve then forms every
  * product with a hopping on that support only (the Sigma_eff term t^H g t costs 2 r c (b or c)
- * instead of 2 b^3, and each backward product contracts over r or c instead of b); entries of
- * H_up outside the support must be zero (the lead decimation and the adjoint use the full
- * blocks, and so does the dense path). */
+ * instead of 2 b^3, and each backward product contracts over r or c instead of b), and so does
+ * negf_lead_selfenergy: the decimation's alpha_n, beta_n keep the support of the lead hopping
+ * (C x R and R x C) through every doubling step, so its six products per step contract over r
+ * or c and form only their r- or c-row blocks, and Sigma_L (Sigma_R) is nonzero only on its
+ * first c (last r) rows and columns.  Entries of H_up outside the support must be zero (the
+ * adjoint uses the full blocks, and so does the dense path). */
 
 typedef struct {
   double eta_lead;       /* imaginary part of z = E + i eta in the lead decimation (eV)   */

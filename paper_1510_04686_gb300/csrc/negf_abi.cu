@@ -61,7 +61,7 @@ bool valid_opt(const negf_options* o) {
 struct LeadWs {
   z64 *eps_s, *eps, *al, *be, *al2, *be2, *g, *ag, *bg, *T1, *M;
   double* scale;
-  int32_t *active, *iters, *item_status, *n_active, *sys;
+  int32_t *active, *iters, *item_status, *n_active, *sys, *act_side;
   EngineWs eng;
 };
 
@@ -84,6 +84,7 @@ void carve_lead(Carver& c, int P, int b, const negf_options* opt, LeadWs& w) {
   w.item_status = c.take<int32_t>(Q);
   w.n_active = c.take<int32_t>(1);
   w.sys = c.take<int32_t>((size_t)P);
+  w.act_side = c.take<int32_t>(Q);
   carve_engine(c.base ? c.base : nullptr, c.off, (int)Q, b, lead_precision(opt, b), w.eng);
 }
 
@@ -178,6 +179,32 @@ negf_status lead_chunk_run(const negf_device* dev, int P, const double* E, const
   CK(launch_fill_i32(s, w.active, Q, 1));
   CK(launch_fill_i32(s, w.iters, Q, 0));
   CK(launch_fill_i32(s, w.item_status, Q, 0));
+  // Interface couplings: tau is nonzero only on its last ir rows R and first ic columns C.  Then
+  // alpha_n keeps the support of alpha_0 (C x R for the left lead, tau_L^H; R x C for the right
+  // lead, tau_R) and beta_n the transposed one through every doubling step, since
+  // alpha' = alpha g alpha and beta' = beta g beta.  With Ra x Ca the support of alpha, the step
+  //   ag[Ra, :] = alpha[Ra, Ca] g[Ca, :]      bg[Ca, :] = beta[Ca, Ra] g[Ra, :]
+  //   eps_s[Ra, Ra], eps[Ra, Ra] += ag[Ra, Ca] beta[Ca, Ra]
+  //   eps[Ca, Ca] += bg[Ca, Ra] alpha[Ra, Ca]
+  //   alpha'[Ra, Ca] = ag[Ra, Ra] alpha[Ra, Ca]      beta'[Ca, Ra] = bg[Ca, Ca] beta[Ca, Ra]
+  // contracts over r or c instead of b; the two leads are separate launches (their supports
+  // differ), each with its own copy of the convergence mask.
+  const int ir = dev->iface_rows > 0 ? dev->iface_rows : b;
+  const int ic = dev->iface_cols > 0 ? dev->iface_cols : b;
+  const bool iface = ir < b || ic < b;
+  const int ra0[2] = {0, b - ir}, nra[2] = {ic, ir};  // alpha rows: C (left), R (right)
+  const int ca0[2] = {b - ir, 0}, nca[2] = {ir, ic};  // alpha columns: R (left), C (right)
+  // item (p, side) of a [P][2][b][b] array, from row r0 and column c0
+  auto sub = [&](z64* base, int side, int r0, int c0) {
+    return BM<double>{base + side * bb + (size_t)r0 * b + c0, (long long)(2 * bb), nullptr, b};
+  };
+  auto subc = [&](z64* base, int side, int r0, int c0) { return cst(sub(base, side, r0, c0)); };
+  if (iface) {
+    CK(launch_fill_i32(s, w.act_side, Q, 1));
+    // alpha', beta' are written on their supports only: the rest of both buffers stays zero
+    CK(cudaMemsetAsync(w.al2, 0, (size_t)Q * bb * sizeof(z64), s));
+    CK(cudaMemsetAsync(w.be2, 0, (size_t)Q * bb * sizeof(z64), s));
+  }
   z64 *al = w.al, *be = w.be, *al2 = w.al2, *be2 = w.be2;
   const double eta = opt->eta_lead;
   int32_t h_active = Q;
@@ -185,25 +212,46 @@ negf_status lead_chunk_run(const negf_device* dev, int P, const double* E, const
     const int32_t* act = w.active;
     CK(launch_zminus(s, Q, b, E, eta, cst(flat(w.eps, bb, b)), flat(w.M, bb, b), act));
     CK(eng.inv(Q, flat(w.M, bb, b), flat(w.g, bb, b), w.item_status, act));
-    CK(eng.gemm(Q, b, b, b, one, cst(flat(al, bb, b)), OP_N, cst(flat(w.g, bb, b)), OP_N, zero,
-                flat(w.ag, bb, b), zero, kNone, act));
-    CK(eng.gemm(Q, b, b, b, one, cst(flat(be, bb, b)), OP_N, cst(flat(w.g, bb, b)), OP_N, zero,
-                flat(w.bg, bb, b), zero, kNone, act));
-    CK(eng.gemm(Q, b, b, b, one, cst(flat(w.ag, bb, b)), OP_N, cst(flat(be, bb, b)), OP_N, zero,
-                flat(w.T1, bb, b), zero, kNone, act));
-    CK(launch_add2(s, Q, b, cst(flat(w.T1, bb, b)), flat(w.eps_s, bb, b), flat(w.eps, bb, b),
-                   act));
-    CK(eng.gemm(Q, b, b, b, one, cst(flat(w.bg, bb, b)), OP_N, cst(flat(al, bb, b)), OP_N, one,
-                flat(w.eps, bb, b), zero, kNone, act));
-    CK(eng.gemm(Q, b, b, b, one, cst(flat(w.ag, bb, b)), OP_N, cst(flat(al, bb, b)), OP_N, zero,
-                flat(al2, bb, b), zero, kNone, act));
-    CK(eng.gemm(Q, b, b, b, one, cst(flat(w.bg, bb, b)), OP_N, cst(flat(be, bb, b)), OP_N, zero,
-                flat(be2, bb, b), zero, kNone, act));
+    if (!iface) {
+      CK(eng.gemm(Q, b, b, b, one, cst(flat(al, bb, b)), OP_N, cst(flat(w.g, bb, b)), OP_N,
+                  zero, flat(w.ag, bb, b), zero, kNone, act));
+      CK(eng.gemm(Q, b, b, b, one, cst(flat(be, bb, b)), OP_N, cst(flat(w.g, bb, b)), OP_N,
+                  zero, flat(w.bg, bb, b), zero, kNone, act));
+      CK(eng.gemm(Q, b, b, b, one, cst(flat(w.ag, bb, b)), OP_N, cst(flat(be, bb, b)), OP_N,
+                  zero, flat(w.T1, bb, b), zero, kNone, act));
+      CK(launch_add2(s, Q, b, cst(flat(w.T1, bb, b)), flat(w.eps_s, bb, b), flat(w.eps, bb, b),
+                     0, b, 0, b, act));
+      CK(eng.gemm(Q, b, b, b, one, cst(flat(w.bg, bb, b)), OP_N, cst(flat(al, bb, b)), OP_N, one,
+                  flat(w.eps, bb, b), zero, kNone, act));
+      CK(eng.gemm(Q, b, b, b, one, cst(flat(w.ag, bb, b)), OP_N, cst(flat(al, bb, b)), OP_N,
+                  zero, flat(al2, bb, b), zero, kNone, act));
+      CK(eng.gemm(Q, b, b, b, one, cst(flat(w.bg, bb, b)), OP_N, cst(flat(be, bb, b)), OP_N,
+                  zero, flat(be2, bb, b), zero, kNone, act));
+    } else {
+      for (int sd = 0; sd < 2; ++sd) {
+        const int32_t* as = w.act_side + (size_t)sd * P;
+        const int r0 = ra0[sd], nr = nra[sd], c0 = ca0[sd], nc = nca[sd];
+        CK(eng.gemm(P, nr, b, nc, one, subc(al, sd, r0, c0), OP_N, subc(w.g, sd, c0, 0), OP_N,
+                    zero, sub(w.ag, sd, r0, 0), zero, kNone, as));
+        CK(eng.gemm(P, nc, b, nr, one, subc(be, sd, c0, r0), OP_N, subc(w.g, sd, r0, 0), OP_N,
+                    zero, sub(w.bg, sd, c0, 0), zero, kNone, as));
+        CK(eng.gemm(P, nr, nr, nc, one, subc(w.ag, sd, r0, c0), OP_N, subc(be, sd, c0, r0), OP_N,
+                    zero, sub(w.T1, sd, r0, r0), zero, kNone, as));
+        CK(eng.gemm(P, nc, nc, nr, one, subc(w.bg, sd, c0, r0), OP_N, subc(al, sd, r0, c0), OP_N,
+                    one, sub(w.eps, sd, c0, c0), zero, kNone, as));
+        CK(eng.gemm(P, nr, nc, nr, one, subc(w.ag, sd, r0, r0), OP_N, subc(al, sd, r0, c0), OP_N,
+                    zero, sub(al2, sd, r0, c0), zero, kNone, as));
+        CK(eng.gemm(P, nc, nr, nc, one, subc(w.bg, sd, c0, c0), OP_N, subc(be, sd, c0, r0), OP_N,
+                    zero, sub(be2, sd, c0, r0), zero, kNone, as));
+      }
+      CK(launch_add2(s, Q, b, cst(flat(w.T1, bb, b)), flat(w.eps_s, bb, b), flat(w.eps, bb, b),
+                     ra0[0], nra[0], ra0[1], nra[1], act));
+    }
     std::swap(al, al2);
     std::swap(be, be2);
     CK(cudaMemsetAsync(w.n_active, 0, sizeof(int32_t), s));
     CK(launch_sr_check(s, Q, b, it, opt->sr_tol, cst(flat(al, bb, b)), cst(flat(be, bb, b)),
-                       w.scale, w.active, w.iters, w.n_active));
+                       w.scale, w.active, w.iters, w.n_active, iface ? w.act_side : nullptr));
     const int chk = opt->sr_host_check;
     if (chk > 0 && it >= 8 && (it % chk == 0 || it == opt->sr_max_iter)) {
       CK(cudaMemcpyAsync(&h_active, w.n_active, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
@@ -218,13 +266,29 @@ negf_status lead_chunk_run(const negf_device* dev, int P, const double* E, const
   BMc<double> tauL{reinterpret_cast<const z64*>(dev->H_up), (long long)((N - 1) * bb), sys, b};
   BMc<double> tauR = tauL;
   tauR.p += (size_t)(N - 2) * bb;
-  BM<double> gL{w.g, (long long)(2 * bb), nullptr, b}, gR{w.g + bb, (long long)(2 * bb), nullptr, b};
-  BM<double> tL{w.T1, (long long)(2 * bb), nullptr, b}, tR{w.T1 + bb, (long long)(2 * bb), nullptr, b};
-  BM<double> sL{sigR, (long long)(2 * bb), nullptr, b}, sRr{sigR + bb, (long long)(2 * bb), nullptr, b};
-  CK(eng.gemm(P, b, b, b, one, cst(gL), OP_N, tauL, OP_N, zero, tL, zero, kNone, nullptr));
-  CK(eng.gemm(P, b, b, b, one, tauL, OP_C, cst(tL), OP_N, zero, sL, zero, kNone, nullptr));
-  CK(eng.gemm(P, b, b, b, one, cst(gR), OP_N, tauR, OP_C, zero, tR, zero, kNone, nullptr));
-  CK(eng.gemm(P, b, b, b, one, tauR, OP_N, cst(tR), OP_N, zero, sRr, zero, kNone, nullptr));
+  if (!iface) {
+    BM<double> gL{w.g, (long long)(2 * bb), nullptr, b}, gR{w.g + bb, (long long)(2 * bb), nullptr, b};
+    BM<double> tL{w.T1, (long long)(2 * bb), nullptr, b}, tR{w.T1 + bb, (long long)(2 * bb), nullptr, b};
+    BM<double> sL{sigR, (long long)(2 * bb), nullptr, b}, sRr{sigR + bb, (long long)(2 * bb), nullptr, b};
+    CK(eng.gemm(P, b, b, b, one, cst(gL), OP_N, tauL, OP_N, zero, tL, zero, kNone, nullptr));
+    CK(eng.gemm(P, b, b, b, one, tauL, OP_C, cst(tL), OP_N, zero, sL, zero, kNone, nullptr));
+    CK(eng.gemm(P, b, b, b, one, cst(gR), OP_N, tauR, OP_C, zero, tR, zero, kNone, nullptr));
+    CK(eng.gemm(P, b, b, b, one, tauR, OP_N, cst(tR), OP_N, zero, sRr, zero, kNone, nullptr));
+  } else {
+    // with T = tau[R, C]:  Sigma_L[C, C] = T^H g_L[R, R] T,  Sigma_R[R, R] = T g_R[C, C] T^H
+    tauL.p += (size_t)(b - ir) * b;
+    tauR.p += (size_t)(b - ir) * b;
+    const int R0 = b - ir;
+    CK(cudaMemsetAsync(sigR, 0, (size_t)Q * bb * sizeof(z64), s));
+    CK(eng.gemm(P, ir, ic, ir, one, subc(w.g, 0, R0, R0), OP_N, tauL, OP_N, zero,
+                sub(w.T1, 0, R0, 0), zero, kNone, nullptr));
+    CK(eng.gemm(P, ic, ic, ir, one, tauL, OP_C, subc(w.T1, 0, R0, 0), OP_N, zero,
+                sub(sigR, 0, 0, 0), zero, kNone, nullptr));
+    CK(eng.gemm(P, ic, ir, ic, one, subc(w.g, 1, 0, 0), OP_N, tauR, OP_C, zero,
+                sub(w.T1, 1, 0, R0), zero, kNone, nullptr));
+    CK(eng.gemm(P, ir, ir, ic, one, tauR, OP_N, subc(w.T1, 1, 0, R0), OP_N, zero,
+                sub(sigR, 1, R0, R0), zero, kNone, nullptr));
+  }
   CK(launch_gamma(s, Q, b, cst(flat(sigR, bb, b)), flat(w.M, bb, b), nullptr));
   CK(launch_lead_lesser(s, Q, b, E, opt->mu_L, opt->mu_R, opt->kT, cst(flat(w.M, bb, b)),
                         flat(sigL, bb, b)));

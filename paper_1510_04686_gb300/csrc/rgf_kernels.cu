@@ -223,24 +223,28 @@ __global__ void k_zminus(int b, const double* E, double eta, BMc<double> X, BM<d
   }
 }
 
-__global__ void k_add2(int b, BMc<double> T1, BM<double> A1, BM<double> A2,
-                       const int32_t* active) {
+__global__ void k_add2(int b, BMc<double> T1, BM<double> A1, BM<double> A2, int o0, int n0,
+                       int o1, int n1, const int32_t* active) {
+  // A1 += T1, A2 += T1 on the square block [o, o + n)^2 of item q (side q & 1 picks o, n)
   const int q = blockIdx.y;
   if (active && !active[q]) return;
-  const z64* t = bat(T1, q);
-  z64* a = bat(A1, q);
-  z64* c = bat(A2, q);
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (long long)b * b;
+  const int o = (q & 1) ? o1 : o0, n = (q & 1) ? n1 : n0;
+  const long long base = (long long)o * b + o;
+  const z64* t = bat(T1, q) + base;
+  z64* a = bat(A1, q) + base;
+  z64* c = bat(A2, q) + base;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < (long long)n * n;
        k += (long long)gridDim.x * blockDim.x) {
-    z64 v = t[k];
-    a[k] = a[k] + v;
-    c[k] = c[k] + v;
+    const long long e = (k / n) * b + (k % n);
+    z64 v = t[e];
+    a[e] = a[e] + v;
+    c[e] = c[e] + v;
   }
 }
 
 __global__ void k_sr_check(int b, int it, double tol, BMc<double> al, BMc<double> be,
                            const double* scale, int32_t* active, int32_t* iters,
-                           int32_t* n_active) {
+                           int32_t* n_active, int32_t* by_side) {
   const int q = blockIdx.x;
   if (!active[q]) return;
   __shared__ double sh[32];
@@ -256,6 +260,8 @@ __global__ void k_sr_check(int b, int it, double tol, BMc<double> al, BMc<double
     if (m < tol * scale[q]) {
       active[q] = 0;
       iters[q] = it;
+      // per-side copy of the mask: by_side[side * P + p] for q = 2 p + side
+      if (by_side) by_side[(q & 1) * (gridDim.x >> 1) + (q >> 1)] = 0;
     } else {
       atomicAdd(n_active, 1);
     }
@@ -409,15 +415,16 @@ cudaError_t launch_zminus(cudaStream_t s, int P2, int b, const double* E, double
   return cudaGetLastError();
 }
 cudaError_t launch_add2(cudaStream_t s, int P2, int b, BMc<double> T1, BM<double> A1,
-                        BM<double> A2, const int32_t* active) {
-  k_add2<<<grid2((long long)b * b, P2), kT, 0, s>>>(b, T1, A1, A2, active);
+                        BM<double> A2, int o0, int n0, int o1, int n1, const int32_t* active) {
+  const int n = n0 > n1 ? n0 : n1;
+  k_add2<<<grid2((long long)n * n, P2), kT, 0, s>>>(b, T1, A1, A2, o0, n0, o1, n1, active);
   count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_sr_check(cudaStream_t s, int P2, int b, int it, double tol, BMc<double> al,
                             BMc<double> be, const double* scale, int32_t* active,
-                            int32_t* iters, int32_t* n_active) {
-  k_sr_check<<<P2, kT, 0, s>>>(b, it, tol, al, be, scale, active, iters, n_active);
+                            int32_t* iters, int32_t* n_active, int32_t* by_side) {
+  k_sr_check<<<P2, kT, 0, s>>>(b, it, tol, al, be, scale, active, iters, n_active, by_side);
   count_launch();
   return cudaGetLastError();
 }

@@ -30,11 +30,14 @@ cudaError_t launch_sr_init(cudaStream_t s, int P2, int b, int N, BMc<double> Hd,
                            double* scale);
 cudaError_t launch_zminus(cudaStream_t s, int P2, int b, const double* E, double eta,
                           BMc<double> X, BM<double> M, const int32_t* active);
+// A1 += T1 and A2 += T1 on the square block [o, o + n)^2 of each item: (o0, n0) for the even
+// (left-lead) items q = 2 p, (o1, n1) for the odd (right-lead) ones.
 cudaError_t launch_add2(cudaStream_t s, int P2, int b, BMc<double> T1, BM<double> A1,
-                        BM<double> A2, const int32_t* active);
+                        BM<double> A2, int o0, int n0, int o1, int n1, const int32_t* active);
+// by_side (nullable, [2][P2 / 2]): items that converge also clear by_side[side][p], q = 2 p + side.
 cudaError_t launch_sr_check(cudaStream_t s, int P2, int b, int it, double tol, BMc<double> al,
                             BMc<double> be, const double* scale, int32_t* active,
-                            int32_t* iters, int32_t* n_active);
+                            int32_t* iters, int32_t* n_active, int32_t* by_side);
 cudaError_t launch_lead_lesser(cudaStream_t s, int P2, int b, const double* E, double mu_L,
                                double mu_R, double kT_, BMc<double> Gam, BM<double> Les);
 cudaError_t launch_sr_status(cudaStream_t s, int P, const int32_t* active,
