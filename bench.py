@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--tc-config", type=int, default=None,
                     help="tensor-core GEMM configuration (default: autotuned per block size "
                          "and batch for the rgf workload, the library default otherwise)")
+    ap.add_argument("--scba-sigma", choices=["diag", "atom"], default="diag",
+                    help="--workload scba: orbital-diagonal or atom-block (10 x 10) self-energies")
     ap.add_argument("--iface-orbitals", type=int, default=100,
                     help="rows and columns of the hopping support in --workload iface")
     ap.add_argument("--gemm-b", type=int, default=400)
@@ -258,9 +260,13 @@ def run_side(args):
         D = negf.Device(torch.as_tensor(dev.D[None], device=dvc), torch.as_tensor(dev.T[None], device=dvc))
         Et = torch.as_tensor(E, device=dvc)
         st = torch.zeros(nE, dtype=torch.int32, device=dvc)
-        opt = negf.options(precision=negf.PREC_MIXED, chunk=min(nE, 128))
+        atom = args.scba_sigma == "atom"
+        opt = negf.options(precision=negf.PREC_MIXED, chunk=min(nE, 128),
+                           sigma_structure=negf.SIGMA_ATOM_BLOCK if atom else
+                           negf.SIGMA_ORBITAL_DIAG, atom_orbitals=10)
+        nS = N * b * negf.sigma_width(opt)  # entries of a self-energy row
         lead = negf.lead_selfenergy(D, Et, st, opt)
-        sR = torch.zeros((nE, N * b), dtype=torch.complex128, device=dvc)
+        sR = torch.zeros((nE, nS), dtype=torch.complex128, device=dvc)
         sL = torch.zeros_like(sR)
         wk = torch.ones(1, dtype=torch.float64, device=dvc)
         n0 = 1.0 / (np.exp(prm["hw"] / prm["kT"]) - 1.0)
@@ -269,7 +275,7 @@ def run_side(args):
         def born():
             out = negf.rgf_solve(D, Et, st, lead["sigma_R"], lead["sigma_L"], opt, scat_R=sR,
                                  scat_L=sL, diag=True, outputs=("density", "current"))
-            d = negf.scba_step(out["diagGR"].reshape(1, nE, N * b), out["diagGL"].reshape(1, nE, N * b),
+            d = negf.scba_step(out["diagGR"].reshape(1, nE, nS), out["diagGL"].reshape(1, nE, nS),
                                wk, sR, sL, prm["D_ac"], prm["D_op"],
                                int(round(prm["hw"] / prm["dE"])), n0)
             deltas.append(d)
@@ -278,7 +284,9 @@ def run_side(args):
         line.update(metric="SCBA point-iterations/s (RGF with phonon self-energies + Born update)",
                     value=nE * args.steps / (ms / 1e3), unit="point-iterations/s",
                     ms_per_step=ms / args.steps, dtype="bf16-slices->fp32 (fp64 storage)",
-                    config={"workload": f"SCBA N=70 b=600, energies 0..{nE - 1} of the 5 meV grid",
+                    config={"workload": f"SCBA N=70 b=600, energies 0..{nE - 1} of the 5 meV grid, "
+                                        + ("atom-block (10 x 10) self-energies" if atom else
+                                           "orbital-diagonal self-energies"),
                             "D_ac": 0.01, "D_op": 0.01, "hw_steps": 12,
                             "last_delta": float(deltas[-1].item())})
     elif args.workload == "adjoint":

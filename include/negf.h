@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define NEGF_ABI_VERSION 2
+#define NEGF_ABI_VERSION 3
 
 typedef enum {
   NEGF_OK = 0,
@@ -84,12 +84,24 @@ typedef enum {
   NEGF_PREC_MIXED_40 = 2, /* tensor cores, 40-bit operand values (cheaper, less accurate)     */
   NEGF_PREC_MIXED_56 = 3  /* tensor cores, 56-bit operand values (FP64-class products)        */
 } negf_precision;
+
 /* negf_options.lead_precision: FP64 when `precision` is FP64, else NEGF_PREC_MIXED_56 (or
  * NEGF_PREC_MIXED for blocks beyond its exact range).  The
  * decimation of a lead whose finite segments have near-singular (z - eps) blocks amplifies the
  * rounding of its early steps by up to ~1e9 (measured on the benchmark device); 56-bit products
  * keep its error at the level of an FP64 decimation. */
 #define NEGF_PREC_AUTO (-1)
+
+/* Structure of the scattering self-energies of Eqs. 4-6 (negf_options.sigma_structure).  The
+ * Born update is linear in diag G entry by entry, so the same update applies to every entry
+ * of a block.
+ *   NEGF_SIGMA_ORBITAL_DIAG: Sigma_scat is diagonal (one value per orbital), built from the
+ *     diagonals of G^R, G^< (default).
+ *   NEGF_SIGMA_ATOM_BLOCK: Sigma_scat is block-diagonal with one A x A block per atom
+ *     (A = negf_options.atom_orbitals consecutive orbitals of a slab), built from the same
+ *     A x A diagonal blocks of G^R, G^<.  Rows then hold N b A entries: entry (r, c) of slab
+ *     i, r and c in the same atom, at i b A + r A + (c mod A). */
+typedef enum { NEGF_SIGMA_ORBITAL_DIAG = 0, NEGF_SIGMA_ATOM_BLOCK = 1 } negf_sigma_structure;
 
 /* Block-tridiagonal device Hamiltonians H(k) of n_sys systems (transverse k x alloy sample).
  * H_diag[s][i]  = H_ii        (Hermitian b x b),  s < n_sys, i < n_slabs
@@ -143,11 +155,16 @@ typedef struct {
                             all, run only for blocks whose residual max |I - M X| is still
                             above 2^-24; a block still above it after refine_max steps is
                             inverted again by FP64 Gauss-Jordan (default 6, range 0-16)      */
+  int32_t sigma_structure; /* negf_sigma_structure of scat_R/L and diagGR/GL (default
+                            NEGF_SIGMA_ORBITAL_DIAG)                                        */
+  int32_t atom_orbitals; /* A: orbitals per atom block under NEGF_SIGMA_ATOM_BLOCK, 1..64,
+                            dividing b (default 10)                                          */
 } negf_options;
 
 /* Fill `opt` with the defaults (eta 1e-6 in leads and device, mu_L = +0.1, mu_R = -0.1,
  * kT = 0.025852, sr_tol = 1e-13, sr_max_iter = 100, FP64, refine_steps = 2, chunk = 0,
- * sr_host_check = 4, adjoint_segment = 0, lead_precision = NEGF_PREC_AUTO, refine_max = 6). */
+ * sr_host_check = 4, adjoint_segment = 0, lead_precision = NEGF_PREC_AUTO, refine_max = 6,
+ * sigma_structure = NEGF_SIGMA_ORBITAL_DIAG, atom_orbitals = 10). */
 void negf_default_options(negf_options* opt);
 
 int32_t negf_abi_version(void);
@@ -192,9 +209,10 @@ negf_status negf_lead_selfenergy(const negf_device* dev, int32_t n_pts, const do
  *   V           device double [N][b] (nullable = 0): on-site potential (the e Phi of Eq. 1),
  *               added to the diagonal of H_ii for every point
  *   sigma_R/L   device complex128 [n_pts][2][b][b]: lead self-energies (negf_lead_selfenergy)
- *   scat_R/L    device complex128 [n_rows][N*b] (nullable = ballistic): orbital-diagonal
- *               phonon self-energies Sigma^R, Sigma^< of Eqs. 4-6; point p uses row
- *               e_idx[p] (e_idx nullable = row p, and then n_rows must be >= n_pts)
+ *   scat_R/L    device complex128 [n_rows][N*b*A] (nullable = ballistic): phonon
+ *               self-energies Sigma^R, Sigma^< of Eqs. 4-6, orbital-diagonal (A = 1) or
+ *               atom blocks (A = atom_orbitals; layout at negf_sigma_structure); point p uses
+ *               row e_idx[p] (e_idx nullable = row p, and then n_rows must be >= n_pts)
  *   density     device double [n_pts][N*b] out (nullable): n_j(E) = Im G^<_jj / (2 pi)
  *   current     device double [n_pts][N-1] out (nullable): bond current
  *               j_i(E) = 2 Re Tr[H_{i,i+1} G^<_{i+1,i}] (Eq. 8, per spin, units 1/h)
@@ -202,8 +220,10 @@ negf_status negf_lead_selfenergy(const negf_device* dev, int32_t n_pts, const do
  *               T(E) = Tr[Gamma_R A_NN] - Tr[Gamma_R G_NN Gamma_R G_NN^H]  (exact when
  *               ballistic; with scattering it is the flux into the right lead per unit
  *               occupation difference of all other sources)
- *   diagGR/GL   device complex128 [n_pts][N*b] out (nullable): diag G^R, diag G^< for the
- *               self-consistent Born step (negf_scba_step)
+ *   diagGR/GL   device complex128 [n_pts][N*b*A] out (nullable): diag G^R, diag G^< (A = 1)
+ *               or their atom diagonal blocks (same layout as scat_R/L) for the
+ *               self-consistent Born step (negf_scba_step, with n_orb = N b A)
+ *   Returns NEGF_ERR_ARG when sigma_structure is invalid or A does not divide b.
  *   status      device int32 [n_pts] out                                                 */
 negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* E,
                            const int32_t* sys_idx, const double* V, const double* sigma_R,
@@ -214,7 +234,8 @@ negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* 
                            double* diagGL, int32_t* status, void* ws, size_t ws_bytes,
                            void* stream);
 
-/* One self-consistent Born update of the orbital-diagonal phonon self-energies (Eqs. 4-6):
+/* One self-consistent Born update of the phonon self-energies (Eqs. 4-6), entry by entry
+ * (orbital diagonals, or every entry of the atom blocks with n_orb = N b A):
  *   Sigma_ac^{R,<}(E_j) = D_ac sum_k w_k dG^{R,<}(k, E_j)                                (4)
  *   Sigma_op^<(E_j) = D_op sum_k w_k [(1+n0) dG^<(k,E_{j+s}) + n0 dG^<(k,E_{j-s})]       (5)
  *   Sigma_op^R(E_j) = D_op sum_k w_k [(1+n0) dG^R(k,E_{j-s}) + n0 dG^R(k,E_{j+s})

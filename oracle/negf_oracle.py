@@ -12,7 +12,9 @@ Conventions (paper, Eqs. 1-8, "Overview"/"Claims" sections):
   * z = E + i*eta; the on-site potential V (eV, per orbital, ``[N, b]``) enters Eq. (1) as
     H_ii + diag(V_i) (the e*Phi term);
   * scattering self-energies of Eqs. (4)-(6) are orbital-diagonal: ``sR[i]``/``sL[i]`` are ``[b]``
-    complex vectors for slab i (the paper's "diag G");
+    complex vectors for slab i (the paper's "diag G"), or block-diagonal with one A x A block
+    per atom, given as a ``[b, b]`` matrix per slab (``atom_block_matrix``); the Born update is
+    the same linear map applied to every entry of diag G or of its atom blocks;
   * leads are semi-infinite periodic copies of the end slabs (left: cell H_11, hopping H_12;
     right: cell H_NN, hopping H_{N-1,N}); Sigma^< = i f Gamma with Gamma = i(Sigma - Sigma^H);
   * density per orbital and energy  n_j(E) = Im G^<_jj / (2 pi)            (Eq. 7 integrand),
@@ -136,10 +138,15 @@ def dense_self_energies(N, b, leads, sR=None, sL=None):
     SL[:b, :b] += leads["lesL"]
     SR[(N - 1) * b:, (N - 1) * b:] += leads["sigR"]
     SL[(N - 1) * b:, (N - 1) * b:] += leads["lesR"]
-    if sR is not None:
-        SR[np.diag_indices(N * b)] += np.asarray(sR).reshape(-1)
-    if sL is not None:
-        SL[np.diag_indices(N * b)] += np.asarray(sL).reshape(-1)
+    for S, X in ((SR, sR), (SL, sL)):
+        if X is None:
+            continue
+        X = np.asarray(X)
+        if X.ndim == 3:  # one b x b matrix per slab (block-diagonal scattering)
+            for i in range(N):
+                S[i * b:(i + 1) * b, i * b:(i + 1) * b] += X[i]
+        else:
+            S[np.diag_indices(N * b)] += X.reshape(-1)
     return SR, SL
 
 
@@ -184,10 +191,11 @@ def rgf(Hd, Hu, E, eta, V, leads, sR=None, sL=None):
         S = np.zeros((b, b), dtype=np.complex128)
         if V is not None:
             M = M - np.diag(np.asarray(V[i], dtype=np.float64))
+        # scattering self-energy of slab i: a diagonal (vector) or a b x b matrix
         if sR is not None:
-            M = M - np.diag(sR[i])
+            M = M - (sR[i] if np.ndim(sR[i]) == 2 else np.diag(sR[i]))
         if sL is not None:
-            S = S + np.diag(sL[i])
+            S = S + (sL[i] if np.ndim(sL[i]) == 2 else np.diag(sL[i]))
         if i == 0:
             M = M - leads["sigL"]
             S = S + leads["lesL"]
@@ -219,6 +227,28 @@ def rgf(Hd, Hu, E, eta, V, leads, sR=None, sL=None):
 # ----------------------------------------------------------------------------------------------
 # Observables (Eqs. 7-8 integrands, transmission)
 # ----------------------------------------------------------------------------------------------
+def atom_blocks(X, A):
+    """The A x A diagonal blocks of a b x b matrix X as a row of b A entries: entry (r, c), r and
+    c in the same atom (orbitals [A a, A a + A)), at r A + (c mod A)."""
+    b = X.shape[0]
+    out = np.zeros(b * A, dtype=np.complex128)
+    for r in range(b):
+        a0 = (r // A) * A
+        for c in range(a0, a0 + A):
+            out[r * A + (c - a0)] = X[r, c]
+    return out
+
+
+def atom_block_matrix(row, b, A):
+    """Inverse of atom_blocks: the b x b block-diagonal matrix with the A x A blocks of `row`."""
+    X = np.zeros((b, b), dtype=np.complex128)
+    for r in range(b):
+        a0 = (r // A) * A
+        for c in range(a0, a0 + A):
+            X[r, c] = row[r * A + (c - a0)]
+    return X
+
+
 def density_from_blocks(GL):
     """n_j(E) = Im G^<_jj / (2 pi) for every orbital, slab-major ``[N*b]``."""
     return np.concatenate([np.imag(np.diag(x)) for x in GL]) / (2.0 * np.pi)

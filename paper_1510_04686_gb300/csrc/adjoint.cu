@@ -163,6 +163,7 @@ struct AdjArgs {
   double* Vbar;         // [N b]
   bool accumulate;
   int32_t* status;
+  int A;  // scattering self-energy block width (1: orbital-diagonal)
 };
 
 negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_t s) {
@@ -205,7 +206,8 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   z64** T = w.t;
   auto has_src = [&](int i) { return i == 0 || i == N - 1 || a.scatL != nullptr; };
   auto build_src = [&](int i, z64* out) -> cudaError_t {
-    return launch_source(s, P, b, a.scatL ? a.scatL + (size_t)i * b : nullptr, NB, erow,
+    return launch_source(s, P, b, a.scatL ? a.scatL + (size_t)i * b * a.A : nullptr,
+                         (long long)NB * a.A, a.A, erow,
                          i == 0 ? SigL_L : none, i == N - 1 ? SigR_L : none, F(out), nullptr);
   };
   const double eta = a.opt->eta_device;
@@ -253,7 +255,8 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
         Y = Fc(T[0]);
       }
       CK(launch_assemble(s, P, b, a.E, eta, Hd(i), a.V ? a.V + (size_t)i * b : nullptr,
-                         a.scatR ? a.scatR + (size_t)i * b : nullptr, NB, erow, Y, b,
+                         a.scatR ? a.scatR + (size_t)i * b * a.A : nullptr,
+                         (long long)NB * a.A, a.A, erow, Y, b,
                          i == 0 ? SigL_R : none, i == N - 1 ? SigR_R : none, F(T[1]), nullptr));
       CK(eng.inv(P, F(T[1]), F(gF(i)), a.status, nullptr));
       bool prev = false;
@@ -488,9 +491,11 @@ extern "C" negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, c
   if (!(opt->kT > 0.0) || opt->refine_steps < 0 || opt->refine_steps > 8 || opt->chunk < 0 ||
       opt->adjoint_segment < 0 || opt->refine_max < 0 || opt->refine_max > 16)
     return NEGF_ERR_ARG;
+  if (!sigma_valid(opt, dev->block)) return NEGF_ERR_ARG;
   if (!V_bar) return NEGF_ERR_ARG;
   const int b = dev->block, N = dev->n_slabs;
   const size_t NB = (size_t)N * b;
+  const int A = sigma_width(opt);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (n_pts == 0) {
     return cudaMemsetAsync(V_bar, 0, NB * sizeof(double), s) == cudaSuccess ? NEGF_OK : NEGF_ERR_CUDA;
@@ -514,8 +519,11 @@ extern "C" negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, c
     a.sigL = reinterpret_cast<const z64*>(sigma_L) + (size_t)p0 * 2 * bb;
     a.e_idx = e_idx ? e_idx + p0 : nullptr;
     a.n_rows = n_rows;
-    a.scatR = scat_R ? reinterpret_cast<const z64*>(scat_R) + (e_idx ? 0 : (size_t)p0 * NB) : nullptr;
-    a.scatL = scat_L ? reinterpret_cast<const z64*>(scat_L) + (e_idx ? 0 : (size_t)p0 * NB) : nullptr;
+    a.scatR = scat_R ? reinterpret_cast<const z64*>(scat_R) + (e_idx ? 0 : (size_t)p0 * NB * A)
+                     : nullptr;
+    a.scatL = scat_L ? reinterpret_cast<const z64*>(scat_L) + (e_idx ? 0 : (size_t)p0 * NB * A)
+                     : nullptr;
+    a.A = A;
     a.opt = opt;
     a.nbar = density_bar ? density_bar + (size_t)p0 * NB : nullptr;
     a.jbar = (current_bar && N > 1) ? current_bar + (size_t)p0 * (N - 1) : nullptr;

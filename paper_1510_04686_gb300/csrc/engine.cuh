@@ -43,6 +43,16 @@ inline int prec_bits(int p) {
 int lead_precision(const negf_options* o, int b);
 // Newton-Schulz steps of the mixed-form inverse: always refine_steps, at most
 // max(refine_steps, refine_max).
+// Width A of the scattering self-energy blocks: 1 (orbital-diagonal) or the atom block size.
+inline int sigma_width(const negf_options* o) {
+  return o->sigma_structure == NEGF_SIGMA_ATOM_BLOCK ? o->atom_orbitals : 1;
+}
+// Valid sigma structure fields for blocks of b orbitals (b a whole number of atom blocks).
+inline bool sigma_valid(const negf_options* o, int b) {
+  if (o->sigma_structure == NEGF_SIGMA_ORBITAL_DIAG) return true;
+  if (o->sigma_structure != NEGF_SIGMA_ATOM_BLOCK) return false;
+  return o->atom_orbitals >= 1 && o->atom_orbitals <= 64 && b % o->atom_orbitals == 0;
+}
 inline int refine_limit(const negf_options* o) {
   return o->refine_max > o->refine_steps ? o->refine_max : o->refine_steps;
 }

@@ -54,6 +54,8 @@ bool valid_opt(const negf_options* o) {
   if (o->refine_steps < 0 || o->refine_steps > 8 || o->chunk < 0) return false;
   if (o->refine_max < 0 || o->refine_max > 16) return false;
   if (o->sr_host_check < 0 || o->adjoint_segment < 0) return false;
+  if (o->sigma_structure != NEGF_SIGMA_ORBITAL_DIAG && o->sigma_structure != NEGF_SIGMA_ATOM_BLOCK)
+    return false;
   return true;
 }
 
@@ -316,6 +318,7 @@ struct RgfArgs {
   double* transmission;
   z64* dGR;
   z64* dGL;
+  int A;  // scattering self-energy block width (1: orbital-diagonal)
   int32_t* status;
 };
 
@@ -392,7 +395,8 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
       Y = Fc(w.Y);
     }
     CK(launch_assemble(s, P, b, a.E, eta, Hd(i), a.V ? a.V + (size_t)i * b : nullptr,
-                       a.scatR ? a.scatR + (size_t)i * b : nullptr, NB, erow, Y, ic,
+                       a.scatR ? a.scatR + (size_t)i * b * a.A : nullptr, (long long)NB * a.A,
+                       a.A, erow, Y, ic,
                        first ? SigL_R : kNone, last ? SigR_R : kNone, F(w.Mt), nullptr));
     CK(eng.inv(P, F(w.Mt), F(G[i]), a.status, nullptr));
     bool have_prev = false;
@@ -410,7 +414,8 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
     const bool has_src = first || last || a.scatL != nullptr;
     if (has_src) {
       // + g_i S_i g_i^H with S_i = diag(Sigma^<_scat) + lead Sigma^< on the end slabs
-      CK(launch_source(s, P, b, a.scatL ? a.scatL + (size_t)i * b : nullptr, NB, erow,
+      CK(launch_source(s, P, b, a.scatL ? a.scatL + (size_t)i * b * a.A : nullptr,
+                       (long long)NB * a.A, a.A, erow,
                        first ? SigL_L : kNone, last ? SigR_L : kNone, F(w.S), nullptr));
       CK(eng.gemm(P, b, b, b, one, Fc(G[i]), OP_N, Fc(w.S), OP_N, zero, F(w.W), zero, kNone,
                   nullptr));
@@ -431,7 +436,8 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
     CK(launch_transmission(s, P, b, Fc(w.S), Fc(G[N - 1]), Fc(w.W), Fc(w.LW), a.transmission,
                            nullptr));
   }
-  CK(launch_slab_obs(s, P, b, N - 1, NB, Fc(G[N - 1]), Fc(GL[N - 1]), a.density, a.dGR, a.dGL,
+  CK(launch_slab_obs(s, P, b, N - 1, NB, a.A, Fc(G[N - 1]), Fc(GL[N - 1]), a.density, a.dGR,
+                     a.dGL,
                      nullptr));
 
   // ---- backward sweep: G_ii, G^<_ii, G^<_{i+1,i}
@@ -460,7 +466,8 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
                 nullptr));
     CK(launch_antiherm(s, P, b, Fc(w.Mt), F(GL[i]), nullptr));
     std::swap(G[i], spare);
-    CK(launch_slab_obs(s, P, b, i, NB, Fc(G[i]), Fc(GL[i]), a.density, a.dGR, a.dGL, nullptr));
+    CK(launch_slab_obs(s, P, b, i, NB, a.A, Fc(G[i]), Fc(GL[i]), a.density, a.dGR, a.dGL,
+                       nullptr));
   }
   if (a.density) CK(launch_check_finite(s, a.density, NB, P, a.status));
   if (a.current && N > 1) CK(launch_check_finite(s, a.current, N - 1, P, a.status));
@@ -491,6 +498,8 @@ void negf_default_options(negf_options* o) {
   o->adjoint_segment = 0;
   o->lead_precision = NEGF_PREC_AUTO;
   o->refine_max = 6;
+  o->sigma_structure = NEGF_SIGMA_ORBITAL_DIAG;
+  o->atom_orbitals = 10;
 }
 
 int32_t negf_abi_version(void) { return NEGF_ABI_VERSION; }
@@ -565,6 +574,7 @@ negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* 
                            size_t ws_bytes, void* stream) {
   if (!valid_dev(dev) || !valid_opt(opt) || n_pts < 0) return NEGF_ERR_ARG;
   if (scat_R && (e_idx ? n_rows < 1 : n_rows < n_pts)) return NEGF_ERR_ARG;
+  if (!sigma_valid(opt, dev->block)) return NEGF_ERR_ARG;
   if (!engine_supports(opt->precision, dev->block)) return NEGF_ERR_UNSUPPORTED;
   if (n_pts == 0) return NEGF_OK;
   if (!E || !sys_idx || !sigma_R || !sigma_L || !status) return NEGF_ERR_ARG;
@@ -574,6 +584,8 @@ negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* 
   if (!ws || ws_bytes < rgf_bytes(C, b, N, opt)) return NEGF_ERR_NOMEM;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t bb = (size_t)b * b, NB = (size_t)N * b;
+  const int A = sigma_width(opt);
+  const size_t NBA = NB * A;  // entries of a scattering self-energy / diag-block row
   if (cudaMemsetAsync(status, 0, (size_t)n_pts * sizeof(int32_t), s) != cudaSuccess)
     return NEGF_ERR_CUDA;
   for (int p0 = 0; p0 < n_pts; p0 += C) {
@@ -588,14 +600,15 @@ negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* 
     a.e_idx = e_idx ? e_idx + p0 : nullptr;
     a.n_rows = n_rows;
     // without an index the scattering rows follow the points
-    a.scatR = scat_R ? reinterpret_cast<const z64*>(scat_R) + (e_idx ? 0 : (size_t)p0 * NB) : nullptr;
-    a.scatL = scat_L ? reinterpret_cast<const z64*>(scat_L) + (e_idx ? 0 : (size_t)p0 * NB) : nullptr;
+    a.scatR = scat_R ? reinterpret_cast<const z64*>(scat_R) + (e_idx ? 0 : (size_t)p0 * NBA) : nullptr;
+    a.scatL = scat_L ? reinterpret_cast<const z64*>(scat_L) + (e_idx ? 0 : (size_t)p0 * NBA) : nullptr;
     a.opt = opt;
     a.density = density ? density + (size_t)p0 * NB : nullptr;
     a.current = (current && N > 1) ? current + (size_t)p0 * (N - 1) : nullptr;
     a.transmission = transmission ? transmission + p0 : nullptr;
-    a.dGR = diagGR ? reinterpret_cast<z64*>(diagGR) + (size_t)p0 * NB : nullptr;
-    a.dGL = diagGL ? reinterpret_cast<z64*>(diagGL) + (size_t)p0 * NB : nullptr;
+    a.dGR = diagGR ? reinterpret_cast<z64*>(diagGR) + (size_t)p0 * NBA : nullptr;
+    a.dGL = diagGL ? reinterpret_cast<z64*>(diagGL) + (size_t)p0 * NBA : nullptr;
+    a.A = A;
     a.status = status + p0;
     negf_status r = rgf_chunk_run(a, P, static_cast<char*>(ws), s);
     if (r != NEGF_OK) return r;

@@ -36,8 +36,12 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   return r;
 }
 
+// Scattering self-energies are block-diagonal with A x A blocks (A = 1: orbital-diagonal):
+// entry (r, c) of a slab, for r and c in the same block, is sc[r A + c mod A].
+__device__ __forceinline__ bool in_block(int r, int c, int A) { return r / A == c / A; }
+
 __global__ void k_assemble(int b, const double* E, double eta, BMc<double> Hd, const double* V,
-                           const z64* scat, long long scat_stride, const int32_t* e_idx,
+                           const z64* scat, long long scat_stride, int A, const int32_t* e_idx,
                            BMc<double> Y, int ny, BMc<double> SigA, BMc<double> SigB,
                            BM<double> M, const int32_t* active) {
   const int p = blockIdx.y;
@@ -56,8 +60,8 @@ __global__ void k_assemble(int b, const double* E, double eta, BMc<double> Hd, c
     if (r == c) {
       v.re += e - (V ? V[r] : 0.0);
       v.im += eta;
-      if (sc) v = v - sc[r];
     }
+    if (sc && in_block(r, c, A)) v = v - sc[(long long)r * A + c % A];
     if (y && r < ny && c < ny) v = v - y[(long long)r * Y.ld + c];
     if (sa) v = v - sa[(long long)r * SigA.ld + c];
     if (sb) v = v - sb[(long long)r * SigB.ld + c];
@@ -65,8 +69,8 @@ __global__ void k_assemble(int b, const double* E, double eta, BMc<double> Hd, c
   }
 }
 
-__global__ void k_source(int b, const z64* scat, long long scat_stride, const int32_t* e_idx,
-                         BMc<double> SigA, BMc<double> SigB, BM<double> S,
+__global__ void k_source(int b, const z64* scat, long long scat_stride, int A,
+                         const int32_t* e_idx, BMc<double> SigA, BMc<double> SigB, BM<double> S,
                          const int32_t* active) {
   const int p = blockIdx.y;
   if (active && !active[p]) return;
@@ -80,7 +84,7 @@ __global__ void k_source(int b, const z64* scat, long long scat_stride, const in
     z64 v = mkc<double>(0.0, 0.0);
     if (sa) v = v + sa[(long long)r * SigA.ld + c];
     if (sb) v = v + sb[(long long)r * SigB.ld + c];
-    if (sc && r == c) v = v + sc[r];
+    if (sc && in_block(r, c, A)) v = v + sc[(long long)r * A + c % A];
     s[(long long)r * S.ld + c] = v;
   }
 }
@@ -98,18 +102,23 @@ __global__ void k_antiherm(int b, BMc<double> S, BM<double> O, const int32_t* ac
   }
 }
 
-__global__ void k_slab_obs(int b, int i, int nb_tot, BMc<double> G, BMc<double> GL,
+// density from diag G^<; dGR / dGL: the A x A diagonal blocks of G^R, G^< (A = 1: diagonals),
+// entry (r, c) at [p][i b A + r A + c mod A]
+__global__ void k_slab_obs(int b, int i, int nb_tot, int A, BMc<double> G, BMc<double> GL,
                            double* density, z64* dGR, z64* dGL, const int32_t* active) {
   const int p = blockIdx.y;
   if (active && !active[p]) return;
   const z64* g = bat(G, p);
   const z64* gl = bat(GL, p);
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < b; j += gridDim.x * blockDim.x) {
-    const long long o = (long long)p * nb_tot + (long long)i * b + j;
-    z64 a = gl[(long long)j * GL.ld + j];
-    if (density) density[o] = a.im / kTwoPi;
-    if (dGR) dGR[o] = g[(long long)j * G.ld + j];
-    if (dGL) dGL[o] = a;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < b; j += gridDim.x * blockDim.x)
+    if (density)
+      density[(long long)p * nb_tot + (long long)i * b + j] = gl[(long long)j * GL.ld + j].im / kTwoPi;
+  if (!dGR && !dGL) return;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < b * A; j += gridDim.x * blockDim.x) {
+    const int r = j / A, c = (r / A) * A + (j - r * A);
+    const long long o = ((long long)p * nb_tot + (long long)i * b) * A + j;
+    if (dGR) dGR[o] = g[(long long)r * G.ld + c];
+    if (dGL) dGL[o] = gl[(long long)r * GL.ld + c];
   }
 }
 
@@ -352,19 +361,19 @@ inline dim3 grid2(long long work, int P) {
 
 cudaError_t launch_assemble(cudaStream_t s, int P, int b, const double* E, double eta,
                             BMc<double> Hd, const double* V, const z64* scat,
-                            long long scat_stride, const int32_t* e_idx, BMc<double> Y,
+                            long long scat_stride, int A, const int32_t* e_idx, BMc<double> Y,
                             int ny, BMc<double> SigA, BMc<double> SigB, BM<double> M,
                             const int32_t* active) {
-  k_assemble<<<grid2((long long)b * b, P), kT, 0, s>>>(b, E, eta, Hd, V, scat, scat_stride,
+  k_assemble<<<grid2((long long)b * b, P), kT, 0, s>>>(b, E, eta, Hd, V, scat, scat_stride, A,
                                                        e_idx, Y, ny, SigA, SigB, M, active);
   count_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_source(cudaStream_t s, int P, int b, const z64* scat, long long scat_stride,
-                          const int32_t* e_idx, BMc<double> SigA, BMc<double> SigB,
+                          int A, const int32_t* e_idx, BMc<double> SigA, BMc<double> SigB,
                           BM<double> S, const int32_t* active) {
-  k_source<<<grid2((long long)b * b, P), kT, 0, s>>>(b, scat, scat_stride, e_idx, SigA, SigB, S,
-                                                     active);
+  k_source<<<grid2((long long)b * b, P), kT, 0, s>>>(b, scat, scat_stride, A, e_idx, SigA, SigB,
+                                                     S, active);
   count_launch();
   return cudaGetLastError();
 }
@@ -374,10 +383,10 @@ cudaError_t launch_antiherm(cudaStream_t s, int P, int b, BMc<double> S, BM<doub
   count_launch();
   return cudaGetLastError();
 }
-cudaError_t launch_slab_obs(cudaStream_t s, int P, int b, int i, int nb_tot, BMc<double> G,
-                            BMc<double> GL, double* density, z64* dGR, z64* dGL,
+cudaError_t launch_slab_obs(cudaStream_t s, int P, int b, int i, int nb_tot, int A,
+                            BMc<double> G, BMc<double> GL, double* density, z64* dGR, z64* dGL,
                             const int32_t* active) {
-  k_slab_obs<<<grid2(b, P), kT, 0, s>>>(b, i, nb_tot, G, GL, density, dGR, dGL, active);
+  k_slab_obs<<<grid2(b, P), kT, 0, s>>>(b, i, nb_tot, A, G, GL, density, dGR, dGL, active);
   count_launch();
   return cudaGetLastError();
 }

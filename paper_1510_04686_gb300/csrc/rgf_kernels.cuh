@@ -4,18 +4,22 @@
 
 namespace negf {
 
+// scat: the slab's scattering self-energy row (nullable), block-diagonal with A x A blocks
+// (A = 1: orbital-diagonal), entry (r, c) at scat[r A + c mod A]; rows of scat_stride entries
+// selected by e_idx (nullable: row p).
 cudaError_t launch_assemble(cudaStream_t s, int P, int b, const double* E, double eta,
                             BMc<double> Hd, const double* V, const z64* scat,
-                            long long scat_stride, const int32_t* e_idx, BMc<double> Y,
+                            long long scat_stride, int A, const int32_t* e_idx, BMc<double> Y,
                             int ny, BMc<double> SigA, BMc<double> SigB, BM<double> M,
                             const int32_t* active);
 cudaError_t launch_source(cudaStream_t s, int P, int b, const z64* scat, long long scat_stride,
-                          const int32_t* e_idx, BMc<double> SigA, BMc<double> SigB,
+                          int A, const int32_t* e_idx, BMc<double> SigA, BMc<double> SigB,
                           BM<double> S, const int32_t* active);
 cudaError_t launch_antiherm(cudaStream_t s, int P, int b, BMc<double> S, BM<double> O,
                             const int32_t* active);
-cudaError_t launch_slab_obs(cudaStream_t s, int P, int b, int i, int nb_tot, BMc<double> G,
-                            BMc<double> GL, double* density, z64* dGR, z64* dGL,
+// density[p][i b + j] (rows of nb_tot); dGR / dGL: A x A diagonal blocks, [p][(i b + r) A + c mod A]
+cudaError_t launch_slab_obs(cudaStream_t s, int P, int b, int i, int nb_tot, int A,
+                            BMc<double> G, BMc<double> GL, double* density, z64* dGR, z64* dGL,
                             const int32_t* active);
 cudaError_t launch_bond_current(cudaStream_t s, int P, int b, BMc<double> Tm, BMc<double> U,
                                 BMc<double> Q, double* out, long long out_stride,

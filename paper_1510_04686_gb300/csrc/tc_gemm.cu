@@ -208,6 +208,29 @@ __device__ __forceinline__ double f32_scaled(uint32_t xb, int k) {
 // active items, [1] issued BF16 MMA flops (padded tiles, computed slice products).
 __device__ double g_tc_prof[2];
 
+// A scalar coefficient of the epilogue, by the work it needs: 0 zero, 1 one, 2 minus one (sign
+// flips only), 3 real (two multiplies), 4 complex.  FP64 throughput is a small fraction of
+// FP32's on this GPU, so the final pass spends FP64 operations only where the value needs them.
+__device__ __forceinline__ int coef_class(z64 a) {
+  if (a.im != 0.0) return 4;
+  if (a.re == 0.0) return 0;
+  if (a.re == 1.0) return 1;
+  if (a.re == -1.0) return 2;
+  return 3;
+}
+__device__ __forceinline__ z64 coef_mul(int cls, z64 a, z64 x) {
+  switch (cls) {
+    case 1: return x;
+    case 2: return mkc(-x.re, -x.im);
+    case 3: return mkc(a.re * x.re, a.re * x.im);
+    default: return a * x;
+  }
+}
+// |x| of a double as its bit pattern without the sign (orders like |x| for finite values)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
 __device__ __forceinline__ float warp_max_f(float v) {
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
@@ -544,13 +567,13 @@ __global__ void __launch_bounds__(kThreads, MINB)
     const int em = row_ok ? eA[(long long)zA * M + m] : 0;
     const int N = N2 >> 1;
     const int32_t* fBp = fB + (long long)zB * N;
-    const bool use_beta = (beta.re != 0.0 || beta.im != 0.0);
-    const bool unit_alpha = (alpha.re == 1.0 && alpha.im == 0.0);
-    const bool unit_gamma = (gamma.re == 1.0 && gamma.im == 0.0);
+    const int cls_alpha = coef_class(alpha), cls_beta = coef_class(beta);
+    const int cls_gamma = D.p ? coef_class(gamma) : 0;
+    const bool want_max = rmax != nullptr;
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int cbase = half * (NT / 2);
     const uint32_t t_hi = tmem + lane_off + kAccBufs * NT, t_lo = t_hi + NT;
-    float omax = 0.0f;  // largest |Re|, |Im| this thread stores (for rmax)
+    unsigned long long omax = 0ull;  // largest |Re|, |Im| this thread stores (rmax), as bits
     for (int acc = 0; acc < n_exec; ++acc) {
       const int buf = acc % kAccBufs;
       if (!mbar_wait(&accfull[buf], (acc / kAccBufs) & 1, abort_flag)) break;
@@ -607,17 +630,17 @@ __global__ void __launch_bounds__(kThreads, MINB)
               const int rl = it * 4 + (lane >> 3), cj = lane & 7;
               const int mr = m0 + q * 32 + rl, n = nb0 + cj;
               if (mr < M && n < N) {
-                const z64 t = stg[rl * 8 + cj];
-                z64 o = unit_alpha ? t : alpha * t;
+                z64 o = coef_mul(cls_alpha, alpha, stg[rl * 8 + cj]);
                 z64* cp = bat(C, p) + (long long)mr * C.ld + n;
-                if (use_beta) o = o + beta * (*cp);
-                if (D.p) {
-                  const z64 dv = bat(D, p)[(long long)mr * D.ld + n];
-                  o = o + (unit_gamma ? dv : gamma * dv);
-                }
+                if (cls_beta) o = o + coef_mul(cls_beta, beta, *cp);
+                if (cls_gamma)
+                  o = o + coef_mul(cls_gamma, gamma, bat(D, p)[(long long)mr * D.ld + n]);
                 if (add_identity && n == mr) o.re += 1.0;
                 *cp = o;
-                omax = fmaxf(omax, (float)fmax(fabs(o.re), fabs(o.im)));
+                if (want_max) {
+                  const unsigned long long a = abs_bits(o.re), c = abs_bits(o.im);
+                  omax = max(omax, max(a, c));
+                }
               }
             }
             __syncwarp();
@@ -635,7 +658,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
       }
     }
     if (rmax) {  // per-item max |output| (non-negative floats order like their bit patterns)
-      const float wm = warp_max_f(omax);
+      const float wm = warp_max_f((float)__longlong_as_double((long long)omax));
       if (lane == 0 && wm > 0.0f)
         atomicMax(reinterpret_cast<unsigned int*>(rmax + p), __float_as_uint(wm));
     }

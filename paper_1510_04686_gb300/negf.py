@@ -19,6 +19,8 @@ PREC_MIXED = 1       # tensor cores, 48-bit operand values
 PREC_MIXED_40 = 2    # tensor cores, 40-bit operand values
 PREC_MIXED_56 = 3    # tensor cores, 56-bit operand values
 PREC_AUTO = -1       # lead_precision: FP64 for the FP64 form, else 56-bit (48 beyond b = 7008)
+SIGMA_ORBITAL_DIAG = 0  # scattering self-energies: one value per orbital
+SIGMA_ATOM_BLOCK = 1    # scattering self-energies: one atom_orbitals^2 block per atom
 WS_LEAD, WS_RGF, WS_ADJOINT = 0, 1, 2
 
 _STATUS = {
@@ -46,7 +48,14 @@ class _Opt(ctypes.Structure):
                 ("mu_R", c_double), ("kT", c_double), ("sr_tol", c_double),
                 ("sr_max_iter", c_int32), ("precision", c_int32), ("refine_steps", c_int32),
                 ("chunk", c_int32), ("sr_host_check", c_int32), ("adjoint_segment", c_int32),
-                ("lead_precision", c_int32), ("refine_max", c_int32)]
+                ("lead_precision", c_int32), ("refine_max", c_int32),
+                ("sigma_structure", c_int32), ("atom_orbitals", c_int32)]
+
+
+def sigma_width(opt) -> int:
+    """Entries per orbital of a scattering self-energy / diag-G row: 1, or the atom block
+    width under SIGMA_ATOM_BLOCK (rows hold N b A entries)."""
+    return int(opt.atom_orbitals) if opt.sigma_structure == SIGMA_ATOM_BLOCK else 1
 
 
 _LIB = None
@@ -257,9 +266,12 @@ def rgf_solve(dev: Device, E, sys_idx, sigma_R, sigma_L, opt, V=None, scat_R=Non
     _need(sigma_L, torch.complex128, "sigma_L", (n, 2, b, b))
     if V is not None:
         _need(V, torch.float64, "V", (N, b))
+    A = sigma_width(opt)
     if scat_R is not None:
         _need(scat_R, torch.complex128, "scat_R")
         _need(scat_L, torch.complex128, "scat_L", tuple(scat_R.shape))
+        if scat_R.shape[-1] != N * b * A:
+            raise ValueError(f"scat_R rows must hold N*b*{A} entries")
     if e_idx is not None:
         _need(e_idx, torch.int32, "e_idx", (n,))
     dv = E.device
@@ -268,8 +280,8 @@ def rgf_solve(dev: Device, E, sys_idx, sigma_R, sigma_L, opt, V=None, scat_R=Non
     cur = (torch.empty((n, max(N - 1, 0)), dtype=torch.float64, device=dv)
            if "current" in outputs else None)
     tr = torch.empty((n,), dtype=torch.float64, device=dv) if "transmission" in outputs else None
-    dGR = torch.empty((n, N * b), dtype=torch.complex128, device=dv) if diag else None
-    dGL = torch.empty((n, N * b), dtype=torch.complex128, device=dv) if diag else None
+    dGR = torch.empty((n, N * b * A), dtype=torch.complex128, device=dv) if diag else None
+    dGL = torch.empty((n, N * b * A), dtype=torch.complex128, device=dv) if diag else None
     st = torch.empty((n,), dtype=torch.int32, device=dv)
     nb = workspace_size(dev, max(n, 1), opt, WS_RGF)
     ws = _workspace(nb, dv)
@@ -333,6 +345,8 @@ def rgf_adjoint(dev: Device, E, sys_idx, sigma_R, sigma_L, opt, density_bar=None
         _need(current_bar, torch.float64, "current_bar", (n, N - 1))
     if V is not None:
         _need(V, torch.float64, "V", (N, b))
+    if scat_R is not None and scat_R.shape[-1] != N * b * sigma_width(opt):
+        raise ValueError(f"scat_R rows must hold N*b*{sigma_width(opt)} entries")
     dv = E.device
     Vbar = torch.empty((N, b), dtype=torch.float64, device=dv)
     st = torch.empty((n,), dtype=torch.int32, device=dv)

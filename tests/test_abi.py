@@ -37,11 +37,12 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_defaults_and_strings(lib):
-    assert lib.negf_abi_version() == 2
+    assert lib.negf_abi_version() == 3
     o = negf.options()
     assert o.eta_lead == 1e-6 and o.eta_device == 1e-6 and o.sr_max_iter == 100
     assert o.precision == negf.PREC_FP64 and o.refine_steps == 2
     assert o.lead_precision == negf.PREC_AUTO and o.refine_max == 6
+    assert o.sigma_structure == negf.SIGMA_ORBITAL_DIAG and o.atom_orbitals == 10
     for code in range(9):
         assert lib.negf_status_string(code)
     assert lib.negf_status_string(99) == b"unknown status"
@@ -110,7 +111,7 @@ def test_binding_refuses_cpu_tensors():
 
 def test_options_struct_layout():
     # six doubles and eight 32-bit integers, as in include/negf.h
-    assert ctypes.sizeof(B._Opt) == 6 * 8 + 8 * 4
+    assert ctypes.sizeof(B._Opt) == 6 * 8 + 10 * 4
     assert ctypes.sizeof(B._Dev) == 4 * 4 + 2 * 8 + 2 * 4
     o = negf.options()
     assert o.sr_host_check == 4
@@ -228,3 +229,25 @@ def test_interface_support_is_validated(lib):
         d = B._Dev(1, 4, 8, r, 1, 1, c, 0)
         size = lib.negf_workspace_size(ctypes.byref(d), 4, ctypes.byref(o), B.WS_RGF)
         assert (size > 0) == ok, (r, c)
+
+
+def test_sigma_structure_is_validated(lib):
+    """Atom-block scattering self-energies need a known structure and a block width that
+    divides b; the check runs on the host before any device work."""
+    d = _dev(b=40)
+    bad_kind = negf.options(sigma_structure=2)
+    assert lib.negf_workspace_size(ctypes.byref(d), 4, ctypes.byref(bad_kind), B.WS_RGF) == 0
+    fake = ctypes.c_void_p(1 << 40)
+    for A, ok in ((10, True), (8, True), (1, True), (7, False), (0, False), (65, False)):
+        o = negf.options(sigma_structure=negf.SIGMA_ATOM_BLOCK, atom_orbitals=A)
+        assert negf.sigma_width(o) == A
+        if ok:
+            continue
+        r = lib.negf_rgf_solve(ctypes.byref(d), 1, fake, fake, None, fake, fake, None, None,
+                               None, 0, ctypes.byref(o), None, None, None, None, None, fake,
+                               fake, 1 << 40, None)
+        assert r == 1, A
+        r = lib.negf_rgf_adjoint(ctypes.byref(d), 1, fake, fake, None, fake, fake, None, None,
+                                 None, 0, ctypes.byref(o), None, None, fake, fake, fake, 1 << 40,
+                                 None)
+        assert r == 1, A

@@ -60,6 +60,22 @@ def test_zgemm_matches_numpy(prec, M, N, K):
         assert np.all(np.abs(got - ref) <= tol + 1e-300), (opA, opB, np.abs(got - ref).max())
 
 
+@pytest.mark.parametrize("al,be", [(1.0, 0.0), (-1.0, 1.0), (2.0, -1.0), (-0.3, 0.25),
+                                   (0.5j, 1.0), (1.0, 0.6 - 0.8j)])
+def test_zgemm_coefficient_forms(al, be):
+    """Each form of alpha and beta (zero, one, minus one, real, complex) in the tensor-core
+    epilogue gives alpha A B + beta C."""
+    rng = np.random.default_rng(int(abs(al) * 100 + abs(be) * 10))
+    nb, M, N, K = 2, 150, 140, 130
+    A, B, C0 = _rand(rng, (nb, M, K)), _rand(rng, (nb, K, N)), _rand(rng, (nb, M, N))
+    ref = al * (A @ B) + be * C0
+    C = torch.as_tensor(C0.copy(), device="cuda")
+    negf.zgemm(torch.as_tensor(A, device="cuda"), torch.as_tensor(B, device="cuda"), C,
+               alpha=al, beta=be, precision=1)
+    tol = 1e-13 * abs(al) * _bound(A, B, "N", "N") + 1e-15 * np.abs(C0)
+    assert np.all(np.abs(C.cpu().numpy() - ref) <= tol + 1e-300)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_zgemm_shared_operand_and_dynamic_range(prec):
     rng = np.random.default_rng(3)
