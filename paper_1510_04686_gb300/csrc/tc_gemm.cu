@@ -243,6 +243,8 @@ __device__ __forceinline__ float warp_max_f(float v) {
 // A and one half of the B tile (NT / 2 rows of the embedded B), so a stage moves 24 KB per CTA
 // instead of 32 KB, and each CTA's tensor memory receives the accumulator of its own rows.  Both
 // CTAs' loads complete on the even CTA's barrier; the MMA commits arrive on both CTAs' barriers.
+constexpr int kStgLd = 9;  // row stride (complex entries) of the final pass's output staging
+
 template <int NT, int STAGES, int CG, int G, int KPS = 1>
 struct Cfg {
   static_assert(STAGES % G == 0, "stages are released in whole groups");
@@ -254,12 +256,16 @@ struct Cfg {
   static constexpr int kATile = KPS * kABox;                  // a stage holds KPS K chunks
   static constexpr int kBTile = KPS * kBBox;
   static constexpr int kStage = kATile + kBTile;
-  static constexpr int kStagingPerWarp = 32 * 8 * 16;         // 32 rows x 8 complex outputs
+  // 32 rows x 8 complex outputs, rows padded to 9 entries (144 bytes): a lane's 16-byte writes
+  // of its own row then fall in distinct banks across each group of 8 lanes
+  static constexpr int kStagingPerWarp = 32 * kStgLd * 16;
   static constexpr int kStaging = kEpiWarps * kStagingPerWarp;
   // the output staging of the tile's final pass reuses the pipeline stages (every MMA and load
   // of the tile has completed by then)
   static_assert(kStaging <= kStages * kStage, "staging fits the stage memory");
   static constexpr int kSmem = kStages * kStage + 1024 + 256;  // + align + barriers
+  // barriers (per-chunk full, per-group empty, accumulator full / empty) and four words
+  static_assert((kStages * KPS + kGroups + 2 * kAccBufs) * 8 + 16 <= 256, "barrier space");
 };
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -335,8 +341,10 @@ __global__ void __launch_bounds__(kThreads, MINB)
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   z64* staging = reinterpret_cast<z64*>(smem);  // the final pass only (see Cfg)
+  // one "full" barrier per K chunk of a stage: the MMAs of a chunk start as soon as its own
+  // tiles have landed, so a stage's later chunks stream in behind its first MMAs
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * CF::kStage);
-  uint64_t* empty = full + kStages;  // one per group of G stages
+  uint64_t* empty = full + kStages * KPS;  // one per group of G stages
   uint64_t* accfull = empty + CF::kGroups;
   uint64_t* accempty = accfull + kAccBufs;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accempty + kAccBufs);
@@ -353,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
   const int zB = zmodeB == 0 ? p : (zmodeB == 1 ? zidxB[p] : 0);
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1);
+    for (int i = 0; i < kStages * KPS; ++i) mbar_init(&full[i], 1);
     for (int i = 0; i < CF::kGroups; ++i) mbar_init(&empty[i], 1);
     for (int i = 0; i < kAccBufs; ++i) {
       mbar_init(&accfull[i], 1);
@@ -433,28 +441,29 @@ __global__ void __launch_bounds__(kThreads, MINB)
           if (stage % G == 0 && !mbar_wait(&empty[stage / G], phase ^ 1, abort_flag)) break;
           unsigned char* st = smem + stage * CF::kStage;
           const int nch = min(KPS, hi - kc);  // K chunks in this stage
-          if constexpr (CG == 2) {
-            // both CTAs' loads of this stage complete on the even CTA's barrier
-            if (leader) mbar_expect_tx(&full[stage], CG * nch * (CF::kABox + CF::kBBox));
-            const uint32_t fb = map_rank(smem_u32(&full[stage]), 0);
 #pragma unroll
-            for (int j = 0; j < KPS; ++j)
-              if (j < nch) {
-                tma_load_3d_pair(st + j * CF::kABox, &mapA, fb, (kc + j) * kKC, m0,
-                                 zA * S + it.s - 1);
-                tma_load_3d_pair(st + CF::kATile + j * CF::kBBox, &mapB, fb, (kc + j) * kKC,
-                                 n0 + (int)rank * CF::kBRows, zB * S + it.t - 1);
-              }
-          } else {
-            mbar_expect_tx(&full[stage], nch * (CF::kABox + CF::kBBox));
-#pragma unroll
-            for (int j = 0; j < KPS; ++j)
-              if (j < nch) {
-                tma_load_3d(st + j * CF::kABox, &mapA, &full[stage], (kc + j) * kKC, m0,
-                            zA * S + it.s - 1);
-                tma_load_3d(st + CF::kATile + j * CF::kBBox, &mapB, &full[stage], (kc + j) * kKC,
-                            n0, zB * S + it.t - 1);
-              }
+          for (int j = 0; j < KPS; ++j) {
+            uint64_t* fj = &full[stage * KPS + j];
+            if (j >= nch) {
+              // no chunk j in this stage: complete the barrier's phase without data, so that
+              // it stays in step with the stage's phase
+              if (leader) mbar_arrive(fj);
+              continue;
+            }
+            if constexpr (CG == 2) {
+              // both CTAs' loads of this chunk complete on the even CTA's barrier
+              if (leader) mbar_expect_tx(fj, CG * (CF::kABox + CF::kBBox));
+              const uint32_t fb = map_rank(smem_u32(fj), 0);
+              tma_load_3d_pair(st + j * CF::kABox, &mapA, fb, (kc + j) * kKC, m0,
+                               zA * S + it.s - 1);
+              tma_load_3d_pair(st + CF::kATile + j * CF::kBBox, &mapB, fb, (kc + j) * kKC,
+                               n0 + (int)rank * CF::kBRows, zB * S + it.t - 1);
+            } else {
+              mbar_expect_tx(fj, CF::kABox + CF::kBBox);
+              tma_load_3d(st + j * CF::kABox, &mapA, fj, (kc + j) * kKC, m0, zA * S + it.s - 1);
+              tma_load_3d(st + CF::kATile + j * CF::kBBox, &mapB, fj, (kc + j) * kKC, n0,
+                          zB * S + it.t - 1);
+            }
           }
           if (++stage == kStages) {
             stage = 0;
@@ -504,16 +513,16 @@ __global__ void __launch_bounds__(kThreads, MINB)
         bool ok = true;
         const int hi = sched.part_hi[it.kp];
         for (int kc = sched.part_lo[it.kp]; kc < hi; kc += KPS) {
-          if (!mbar_wait(&full[stage], phase, abort_flag)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
           const uint32_t a0 = smem_u32(smem + stage * CF::kStage);
           const int nch = min(KPS, hi - kc);
 #pragma unroll
           for (int j = 0; j < KPS; ++j) {
             if (j >= nch) break;
+            if (!mbar_wait(&full[stage * KPS + j], phase, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
             const uint32_t aj = a0 + j * CF::kABox, bj = a0 + CF::kATile + j * CF::kBBox;
 #pragma unroll
             for (int k = 0; k < kKC / 16; ++k) {
@@ -525,6 +534,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
               acc_on = 1;
             }
           }
+          if (!ok) break;
           if (stage % G == G - 1) {  // last stage of its group: release the group
             if constexpr (CG == 2)
               mma_commit_pair(&empty[stage / G]);
@@ -612,7 +622,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
         } else {
           // Final value of this row's 16 complex outputs, written through a per-warp staging
           // tile so that C, D and the stores are accessed as contiguous 128-byte row segments.
-          z64* stg = staging + warp * (32 * 8);
+          z64* stg = staging + warp * (32 * kStgLd);
 #pragma unroll
           for (int half8 = 0; half8 < CW / 16; ++half8) {
 #pragma unroll
@@ -620,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
               const int j = 16 * half8 + 2 * jj;
               const int n = (n0 + c0 + j) >> 1;
               const int sh = em + (n < N ? fBp[n] : 0) - two_beta;
-              stg[lane * 8 + jj] = mkc(f32_scaled(h[j], sh) + f32_scaled(l[j], sh),
+              stg[lane * kStgLd + jj] = mkc(f32_scaled(h[j], sh) + f32_scaled(l[j], sh),
                                        f32_scaled(h[j + 1], sh) + f32_scaled(l[j + 1], sh));
             }
             __syncwarp();
@@ -630,7 +640,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
               const int rl = it * 4 + (lane >> 3), cj = lane & 7;
               const int mr = m0 + q * 32 + rl, n = nb0 + cj;
               if (mr < M && n < N) {
-                z64 o = coef_mul(cls_alpha, alpha, stg[rl * 8 + cj]);
+                z64 o = coef_mul(cls_alpha, alpha, stg[rl * kStgLd + cj]);
                 z64* cp = bat(C, p) + (long long)mr * C.ld + n;
                 if (cls_beta) o = o + coef_mul(cls_beta, beta, *cp);
                 if (cls_gamma)
