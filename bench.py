@@ -559,7 +559,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": (f"bf16-slices->fp32 (fp64 storage; sweeps {tier_bits(negf, prec)}-bit, "
-                  "leads 56-bit operand values)") if mixed else "f64",
+                  "lead decimation 56/48/40-bit by doubling step)") if mixed else "f64",
         "data": "synthetic",
         "config": {"workload": WORK["name"], "points_per_step": P, "precision": args.precision,
                    "l2": "inputs > L2: each step streams 358 MB of H blocks",

@@ -85,11 +85,14 @@ typedef enum {
   NEGF_PREC_MIXED_56 = 3  /* tensor cores, 56-bit operand values (FP64-class products)        */
 } negf_precision;
 
-/* negf_options.lead_precision: FP64 when `precision` is FP64, else NEGF_PREC_MIXED_56 (or
- * NEGF_PREC_MIXED for blocks beyond its exact range).  The
- * decimation of a lead whose finite segments have near-singular (z - eps) blocks amplifies the
- * rounding of its early steps by up to ~1e9 (measured on the benchmark device); 56-bit products
- * keep its error at the level of an FP64 decimation. */
+/* negf_options.lead_precision = NEGF_PREC_AUTO: FP64 when `precision` is FP64; else a schedule
+ * over the doubling steps of the decimation, 56-bit products for steps 1-8, 48-bit for 9-14 and
+ * 40-bit from step 15 (48-bit for the surface Green's function and Sigma after the loop), or
+ * NEGF_PREC_MIXED throughout for blocks beyond the 56-bit exact range.  The decimation of a
+ * lead whose finite segments have near-singular (z - eps) blocks amplifies the rounding of its
+ * early steps by up to ~1e9 (measured on the benchmark device); 56-bit products keep its error
+ * at the level of an FP64 decimation there, while rounding at later steps is amplified by at
+ * most ~3e4 (steps 5-10) and ~300 (steps >= 15).  A fixed tier applies to every step. */
 #define NEGF_PREC_AUTO (-1)
 
 /* Structure of the scattering self-energies of Eqs. 4-6 (negf_options.sigma_structure).  The

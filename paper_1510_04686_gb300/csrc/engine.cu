@@ -98,6 +98,14 @@ int lead_precision(const negf_options* o, int b) {
   return engine_supports(NEGF_PREC_MIXED_56, b) ? NEGF_PREC_MIXED_56 : NEGF_PREC_MIXED;
 }
 
+int lead_step_precision(const negf_options* o, int b, int it) {
+  const int p = lead_precision(o, b);
+  if (o->lead_precision != NEGF_PREC_AUTO || p != NEGF_PREC_MIXED_56) return p;
+  if (it == 0) return NEGF_PREC_MIXED;
+  if (it <= 8) return NEGF_PREC_MIXED_56;
+  return it <= 14 ? NEGF_PREC_MIXED : NEGF_PREC_MIXED_40;
+}
+
 long long engine_fp64_fallbacks() {
   unsigned long long v = 0;
   if (cudaMemcpyFromSymbol(&v, g_fp64_fallbacks, sizeof(v)) != cudaSuccess) return -1;

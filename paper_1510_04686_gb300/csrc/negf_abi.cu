@@ -212,6 +212,8 @@ negf_status lead_chunk_run(const negf_device* dev, int P, const double* E, const
   int32_t h_active = Q;
   for (int it = 1; it <= opt->sr_max_iter; ++it) {
     const int32_t* act = w.active;
+    // the workspace is carved for lead_precision(opt, b), the widest tier of the schedule
+    eng.prec = lead_step_precision(opt, b, it);
     CK(launch_zminus(s, Q, b, E, eta, cst(flat(w.eps, bb, b)), flat(w.M, bb, b), act));
     CK(eng.inv(Q, flat(w.M, bb, b), flat(w.g, bb, b), w.item_status, act));
     if (!iface) {
@@ -262,6 +264,7 @@ negf_status lead_chunk_run(const negf_device* dev, int P, const double* E, const
     }
   }
   // surface Green's functions g_s = (z - eps_s)^-1 for every item
+  eng.prec = lead_step_precision(opt, b, 0);
   CK(launch_zminus(s, Q, b, E, eta, cst(flat(w.eps_s, bb, b)), flat(w.M, bb, b), nullptr));
   CK(eng.inv(Q, flat(w.M, bb, b), flat(w.g, bb, b), w.item_status, nullptr));
   // left:  Sigma_L = tau_L^H g_L tau_L;  right: Sigma_R = tau_R g_R tau_R^H
