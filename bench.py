@@ -32,10 +32,10 @@ WORK = dict(N=70, b=400, n_E=512, n_k=8, ge_frac=0.1, eta=1e-6, seed=1001,
 METRIC = "RGF energy-points/s (leads + forward/backward sweeps + observables + FP64 quadrature)"
 PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0)
 # DRAM bytes (read + write) of k_tc_gemm per 400 x 400 x 400 complex item from an ncu capture of
-# a 64-item 48-bit launch of tensor-core configuration 18 (806.6 MB read + 149.5 MB written),
+# a 64-item 48-bit launch of tensor-core configuration 18 (803.3 MB read + 149.7 MB written),
 # scaled by the items of a launch; None once the kernel has changed since the capture (the line
 # then reports null).
-TC_DRAM_BYTES_PER_ITEM_B400 = (806.572544e6 + 149.506560e6) / 64
+TC_DRAM_BYTES_PER_ITEM_B400 = (803.316480e6 + 149.674496e6) / 64
 # configurations 18 and 19 run the same launch at b = 400 (one K part under either policy)
 TC_PROFILED_CONFIGS = (18, 19)
 GOLDEN = os.path.join(ROOT, "tests", "golden", "c1_oracle.json")
@@ -69,6 +69,11 @@ def parse():
                          "complex GEMM alone (b x b x b, --gemm-batch items)")
     ap.add_argument("--scba-energies", type=int, default=128)
     ap.add_argument("--adj-slabs", type=int, default=20)
+    ap.add_argument("--adj-segment", type=int, default=0,
+                    help="--workload adjoint: slabs per checkpointed segment (0 = keep all)")
+    ap.add_argument("--adj-iface", type=int, default=0,
+                    help="--workload adjoint: hoppings supported on the last r rows / first r "
+                         "columns (the facing atoms), r orbitals; 0 = dense")
     ap.add_argument("--ragged-points", type=int, default=4,
                     help="energies per (sample, k) system of the ragged workload")
     ap.add_argument("--ragged-samples", type=int, default=16)
@@ -294,10 +299,20 @@ def run_side(args):
         dev, V = w["device"], w["V"]
         N, b = dev.N, dev.b
         rng = np.random.default_rng(4)
-        D = negf.Device(torch.as_tensor(dev.D[None], device=dvc), torch.as_tensor(dev.T[None], device=dvc))
+        T = dev.T
+        iface = None
+        if args.adj_iface > 0:
+            # hoppings only between the facing atoms: the last r rows and first r columns
+            r = args.adj_iface
+            T = T.copy()
+            T[:, :b - r, :] = 0.0
+            T[:, :, r:] = 0.0
+            iface = (r, r)
+        D = negf.Device(torch.as_tensor(dev.D[None], device=dvc), torch.as_tensor(T[None], device=dvc),
+                        iface=iface)
         Et = torch.as_tensor(np.array([0.1]), device=dvc)
         st = torch.zeros(1, dtype=torch.int32, device=dvc)
-        opt = negf.options(precision=negf.PREC_MIXED, chunk=1)
+        opt = negf.options(precision=negf.PREC_MIXED, chunk=1, adjoint_segment=args.adj_segment)
         lead = negf.lead_selfenergy(D, Et, st, opt)
         Vt = torch.as_tensor(V, device=dvc)
         c = torch.as_tensor(rng.normal(size=(1, N * b)), device=dvc)
@@ -311,7 +326,11 @@ def run_side(args):
                     value=args.steps / (ms / 1e3), unit="points/s", ms_per_step=ms / args.steps,
                     dtype="bf16-slices->fp32 (fp64 storage)",
                     config={"workload": f"adjoint, N={N} slabs x 3430 orbitals (343 atoms x 10),"
-                                        " V ~ U(-0.3, 0.3) eV per atom, 1 point"})
+                                        " V ~ U(-0.3, 0.3) eV per atom, 1 point"
+                                        + (f", hoppings on the {args.adj_iface} x "
+                                           f"{args.adj_iface} facing-atom block"
+                                           if args.adj_iface > 0 else ""),
+                            "adjoint_segment": args.adj_segment})
     elif args.workload == "iface":
         # the benchmark device with interface couplings: every hopping block keeps only the
         # orbitals of the 10 facing atoms of each slab (its last 100 rows, first 100 columns)

@@ -131,8 +131,10 @@ typedef struct {
  * negf_lead_selfenergy: the decimation's alpha_n, beta_n keep the support of the lead hopping
  * (C x R and R x C) through every doubling step, so its six products per step contract over r
  * or c and form only their r- or c-row blocks, and Sigma_L (Sigma_R) is nonzero only on its
- * first c (last r) rows and columns.  Entries of H_up outside the support must be zero (the
- * adjoint uses the full blocks, and so does the dense path). */
+ * first c (last r) rows and columns; negf_rgf_adjoint restricts its recomputed sweeps and
+ * every reverse-mode product with a hopping, or with an intermediate of that structure (L, K,
+ * W, LW and their cotangents), in the same way.  Entries of H_up outside the support must be
+ * zero. */
 
 typedef struct {
   double eta_lead;       /* imaginary part of z = E + i eta in the lead decimation (eV)   */

@@ -204,6 +204,32 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   const BMc<double> SigL_L{a.sigL, (long long)(2 * bb), nullptr, b};
   const BMc<double> SigR_L{a.sigL + bb, (long long)(2 * bb), nullptr, b};
   z64** T = w.t;
+  // Interface couplings: t_i is nonzero only on its last ir rows R and first ic columns C
+  // (ir = ic = b: dense, and every view below is the whole block).  Then L = g t lives on the
+  // columns C, K = g t^H and W = G t^H on the columns R, Y = t^H L on C x C, and so do the
+  // cotangents that matter: every product with a hopping, and every product of an intermediate
+  // with that structure, contracts over r or c and forms only the part of its output that
+  // is read later (the other entries of those buffers are never read).
+  const int ir = dev->iface_rows > 0 ? dev->iface_rows : b;
+  const int ic = dev->iface_cols > 0 ? dev->iface_cols : b;
+  const int R0 = b - ir;  // first row of R (C starts at column 0)
+  auto cv = [](BMc<double> X, int c0) {
+    X.p += c0;
+    return X;
+  };
+  auto rv = [](BMc<double> X, int r0) {
+    X.p += (long long)r0 * X.ld;
+    return X;
+  };
+  auto bcv = [](BM<double> X, int c0) {
+    X.p += c0;
+    return X;
+  };
+  auto brv = [](BM<double> X, int r0) {
+    X.p += (long long)r0 * X.ld;
+    return X;
+  };
+  auto tv = [&](BMc<double> H) { return rv(H, R0); };  // the r x c support T of a hopping
   auto has_src = [&](int i) { return i == 0 || i == N - 1 || a.scatL != nullptr; };
   auto build_src = [&](int i, z64* out) -> cudaError_t {
     return launch_source(s, P, b, a.scatL ? a.scatL + (size_t)i * b * a.A : nullptr,
@@ -248,25 +274,27 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
       if (i > 0) {
         // L_{i-1} = g_{i-1} t_{i-1} (kept when slab i - 1 is in the segment);  Y = t^H L
         z64* Lprev = (i - 1 >= lo) ? Lb(i - 1) : T[6];
-        CK(eng.gemm(P, b, b, b, one, Fc(gF(i - 1)), OP_N, Hu(i - 1), OP_N, zero, F(Lprev), zero,
-                    none, nullptr));
-        CK(eng.gemm(P, b, b, b, one, Hu(i - 1), OP_C, Fc(Lprev), OP_N, zero, F(T[0]), zero, none,
-                    nullptr));
+        // L[:, C] = g[:, R] T;  Y[C, C] = T^H L[R, C]
+        CK(eng.gemm(P, b, ic, ir, one, cv(Fc(gF(i - 1)), R0), OP_N, tv(Hu(i - 1)), OP_N, zero,
+                    F(Lprev), zero, none, nullptr));
+        CK(eng.gemm(P, ic, ic, ir, one, tv(Hu(i - 1)), OP_C, rv(Fc(Lprev), R0), OP_N, zero,
+                    F(T[0]), zero, none, nullptr));
         Y = Fc(T[0]);
       }
       CK(launch_assemble(s, P, b, a.E, eta, Hd(i), a.V ? a.V + (size_t)i * b : nullptr,
                          a.scatR ? a.scatR + (size_t)i * b * a.A : nullptr,
-                         (long long)NB * a.A, a.A, erow, Y, b,
+                         (long long)NB * a.A, a.A, erow, Y, ic,
                          i == 0 ? SigL_R : none, i == N - 1 ? SigR_R : none, F(T[1]), nullptr));
       CK(eng.inv(P, F(T[1]), F(gF(i)), a.status, nullptr));
       bool prev = false;
       if (i > 0) {
-        CK(eng.gemm(P, b, b, b, one, Fc(gF(i)), OP_N, Hu(i - 1), OP_C, zero, F(T[2]), zero, none,
-                    nullptr));
-        CK(eng.gemm(P, b, b, b, one, Fc(glF(i - 1)), OP_N, Fc(T[2]), OP_C, zero, F(T[3]), zero,
-                    none, nullptr));
-        CK(eng.gemm(P, b, b, b, one, Fc(T[2]), OP_N, Fc(T[3]), OP_N, zero, F(glF(i)), zero, none,
-                    nullptr));
+        // K[:, R] = g_i[:, C] T^H;  Vt = g^<_{i-1}[:, R] K[:, R]^H;  g^<_i = K[:, R] Vt[R, :]
+        CK(eng.gemm(P, b, ir, ic, one, Fc(gF(i)), OP_N, tv(Hu(i - 1)), OP_C, zero,
+                    bcv(F(T[2]), R0), zero, none, nullptr));
+        CK(eng.gemm(P, b, b, ir, one, cv(Fc(glF(i - 1)), R0), OP_N, cv(Fc(T[2]), R0), OP_C, zero,
+                    F(T[3]), zero, none, nullptr));
+        CK(eng.gemm(P, b, b, ir, one, cv(Fc(T[2]), R0), OP_N, rv(Fc(T[3]), R0), OP_N, zero,
+                    F(glF(i)), zero, none, nullptr));
         prev = true;
       }
       if (has_src(i)) {
@@ -280,14 +308,35 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
       }
     }
     if (hi - 1 <= N - 2)
-      CK(eng.gemm(P, b, b, b, one, Fc(gF(hi - 1)), OP_N, Hu(hi - 1), OP_N, zero, F(Lb(hi - 1)),
-                  zero, none, nullptr));
+      CK(eng.gemm(P, b, ic, ir, one, cv(Fc(gF(hi - 1)), R0), OP_N, tv(Hu(hi - 1)), OP_N, zero,
+                  F(Lb(hi - 1)), zero, none, nullptr));
     if (c + 1 < nseg) {
       CK(cudaMemcpyAsync(S(w.ckg, c + 1), gF(hi - 1), PB * sizeof(z64),
                          cudaMemcpyDeviceToDevice, s));
       CK(cudaMemcpyAsync(S(w.ckgl, c + 1), glF(hi - 1), PB * sizeof(z64),
                          cudaMemcpyDeviceToDevice, s));
     }
+    return NEGF_OK;
+  };
+
+  negf_status r;
+#define RUN(x)                          \
+  do {                                  \
+    if ((r = (x)) != NEGF_OK) return r; \
+  } while (0)
+
+  // W[:, R] = G_{i+1}[:, C] T^H;  LW[:, R] = L[:, C] W[C, R];  Q = G^<_{i+1}[:, C] L[:, C]^H;
+  // U = 2 W[:, R] g^<_i[R, :] + Q  (backward step i, its blocks resident)
+  auto backward_products = [&](int i, z64* Wm, z64* LW, z64* Q, z64* U) -> negf_status {
+    z64* L = Lb(i);
+    CK(eng.gemm(P, b, ir, ic, one, Fc(Gb(i + 1)), OP_N, tv(Hu(i)), OP_C, zero, bcv(F(Wm), R0),
+                zero, none, nullptr));
+    CK(eng.gemm(P, b, ir, ic, one, Fc(L), OP_N, cv(Fc(Wm), R0), OP_N, zero, bcv(F(LW), R0), zero,
+                none, nullptr));
+    CK(eng.gemm(P, b, b, ic, one, Fc(GLb(i + 1)), OP_N, Fc(L), OP_C, zero, F(Q), zero, none,
+                nullptr));
+    CK(eng.gemm(P, b, b, ir, two, cv(Fc(Wm), R0), OP_N, rv(Fc(glF(i)), R0), OP_N, zero, F(U), one,
+                Fc(Q), nullptr));
     return NEGF_OK;
   };
 
@@ -305,17 +354,10 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
     }
     for (int i = top; i >= lo; --i) {
       z64 *Wm = T[0], *LW = T[1], *Q = T[2], *U = T[3];
-      CK(eng.gemm(P, b, b, b, one, Fc(Gb(i + 1)), OP_N, Hu(i), OP_C, zero, F(Wm), zero, none,
-                  nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(Lb(i)), OP_N, Fc(Wm), OP_N, zero, F(LW), zero, none,
-                  nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(LW), OP_N, Fc(gF(i)), OP_N, zero, F(Gb(i)), one,
-                  Fc(gF(i)), nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(GLb(i + 1)), OP_N, Fc(Lb(i)), OP_C, zero, F(Q), zero,
-                  none, nullptr));
-      CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_N, Fc(glF(i)), OP_N, zero, F(U), one, Fc(Q),
-                  nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(Lb(i)), OP_N, Fc(U), OP_N, zero, F(T[4]), one,
+      RUN(backward_products(i, Wm, LW, Q, U));
+      CK(eng.gemm(P, b, b, ir, one, cv(Fc(LW), R0), OP_N, rv(Fc(gF(i)), R0), OP_N, zero,
+                  F(Gb(i)), one, Fc(gF(i)), nullptr));
+      CK(eng.gemm(P, b, b, ic, one, Fc(Lb(i)), OP_N, Fc(U), OP_N, zero, F(T[4]), one,
                   Fc(glF(i)), nullptr));
       CK(launch_antiherm(s, P, b, Fc(T[4]), F(GLb(i)), nullptr));
     }
@@ -326,12 +368,6 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
     }
     return NEGF_OK;
   };
-  negf_status r;
-#define RUN(x)                        \
-  do {                                \
-    if ((r = (x)) != NEGF_OK) return r; \
-  } while (0)
-
   // ------------------------------------------------ forward sweep: checkpoints of every segment
   for (int c = 0; c < nseg; ++c) RUN(forward_segment(c));
   // ------------------------------------------------ backward sweep: checkpoints, top down
@@ -358,42 +394,50 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
     z64 *Wm = T[0], *LW = T[1], *Q = T[2], *U = T[3], *Sb = T[4], *Ub = T[5], *Wb = T[6],
         *Qb = T[7], *LWb = T[8];
     z64* L = Lb(i);
+    z64* Lbar = S(w.Lbar, i);
     // recompute W, LW, Q, U of backward step i
-    CK(eng.gemm(P, b, b, b, one, Fc(Gb(i + 1)), OP_N, Hu(i), OP_C, zero, F(Wm), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(L), OP_N, Fc(Wm), OP_N, zero, F(LW), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(GLb(i + 1)), OP_N, Fc(L), OP_C, zero, F(Q), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_N, Fc(glF(i)), OP_N, zero, F(U), one, Fc(Q), nullptr));
-    // current cotangent: Ubar = Qbar = d_i t_i^H
+    RUN(backward_products(i, Wm, LW, Q, U));
+    // current cotangent: Ubar = Qbar = d_i t_i^H (rows C; every later term of Ubar, Qbar too)
     k_set_dtH<<<g2((long long)bb, P), kT, 0, s>>>(b, Hu(i), a.jbar ? a.jbar + i : nullptr, N - 1, F(Ub));
     k_set_dtH<<<g2((long long)bb, P), kT, 0, s>>>(b, Hu(i), a.jbar ? a.jbar + i : nullptr, N - 1, F(Qb));
     count_launch(2);
-    // G^<_i = AH(g^<_i + L U)
+    // G^<_i = AH(g^<_i + L U):  Lbar[:, C] += Sbar U[C, :]^H,  Ubar[C, :] += L[:, C]^H Sbar
     CK(launch_antiherm(s, P, b, Fc(GLc), F(Sb), nullptr));
     k_axpy<<<(unsigned)std::min<size_t>((PB + kT - 1) / kT, 4096), kT, 0, s>>>((long long)PB, Sb, S(w.glbar, i));
     count_launch();
-    CK(eng.gemm(P, b, b, b, one, Fc(Sb), OP_N, Fc(U), OP_C, one, F(S(w.Lbar, i)), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(L), OP_C, Fc(Sb), OP_N, one, F(Ub), zero, none, nullptr));
-    // U = 2 W g^<_i + Q
-    CK(eng.gemm(P, b, b, b, two, Fc(Ub), OP_N, Fc(glF(i)), OP_C, zero, F(Wb), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, two, Fc(Wm), OP_C, Fc(Ub), OP_N, one, F(S(w.glbar, i)), zero, none, nullptr));
+    CK(eng.gemm(P, b, ic, b, one, Fc(Sb), OP_N, Fc(U), OP_C, one, F(Lbar), zero, none, nullptr));
+    CK(eng.gemm(P, ic, b, b, one, Fc(L), OP_C, Fc(Sb), OP_N, one, F(Ub), zero, none, nullptr));
+    // U = 2 W g^<_i + Q:  Wbar[C, R] = 2 Ubar[C, :] g^<_i[R, :]^H,
+    // g^<bar_i[R, :] += 2 W[C, R]^H Ubar[C, :],  Qbar += Ubar
+    CK(eng.gemm(P, ic, ir, b, two, Fc(Ub), OP_N, rv(Fc(glF(i)), R0), OP_C, zero, bcv(F(Wb), R0),
+                zero, none, nullptr));
+    CK(eng.gemm(P, ir, b, ic, two, cv(Fc(Wm), R0), OP_C, Fc(Ub), OP_N, one,
+                brv(F(S(w.glbar, i)), R0), zero, none, nullptr));
     k_axpy<<<(unsigned)std::min<size_t>((PB + kT - 1) / kT, 4096), kT, 0, s>>>((long long)PB, Ub, Qb);
     count_launch();
-    // Q = G^<_{i+1} L^H
+    // Q = G^<_{i+1} L^H:  G^<bar_{i+1}[C, C] += Qbar[C, :] L[:, C],
+    // Lbar[:, C] += Qbar[C, :]^H G^<_{i+1}[C, C]
     k_seed_density<<<g2((long long)bb, P), kT, 0, s>>>(b, i + 1, NB, a.nbar, F(GLn));
     count_launch();
-    CK(eng.gemm(P, b, b, b, one, Fc(Qb), OP_N, Fc(L), OP_N, one, F(GLn), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(Qb), OP_C, Fc(GLb(i + 1)), OP_N, one, F(S(w.Lbar, i)), zero,
-                none, nullptr));
-    // G_i = g_i + LW g_i
+    CK(eng.gemm(P, ic, ic, b, one, Fc(Qb), OP_N, Fc(L), OP_N, one, F(GLn), zero, none, nullptr));
+    CK(eng.gemm(P, b, ic, ic, one, Fc(Qb), OP_C, Fc(GLb(i + 1)), OP_N, one, F(Lbar), zero, none,
+                nullptr));
+    // G_i = g_i + LW g_i:  LWbar[:, R] = Gbar g_i[R, :]^H,  gbar_i[R, :] += LW[:, R]^H Gbar
     k_axpy<<<(unsigned)std::min<size_t>((PB + kT - 1) / kT, 4096), kT, 0, s>>>((long long)PB, Gc, S(w.gbar, i));
     count_launch();
-    CK(eng.gemm(P, b, b, b, one, Fc(Gc), OP_N, Fc(gF(i)), OP_C, zero, F(LWb), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(LW), OP_C, Fc(Gc), OP_N, one, F(S(w.gbar, i)), zero, none, nullptr));
-    // LW = L W
-    CK(eng.gemm(P, b, b, b, one, Fc(LWb), OP_N, Fc(Wm), OP_C, one, F(S(w.Lbar, i)), zero, none, nullptr));
-    CK(eng.gemm(P, b, b, b, one, Fc(L), OP_C, Fc(LWb), OP_N, one, F(Wb), zero, none, nullptr));
-    // W = G_{i+1} t_i^H
-    CK(eng.gemm(P, b, b, b, one, Fc(Wb), OP_N, Hu(i), OP_N, zero, F(Gn), zero, none, nullptr));
+    CK(eng.gemm(P, b, ir, b, one, Fc(Gc), OP_N, rv(Fc(gF(i)), R0), OP_C, zero, bcv(F(LWb), R0),
+                zero, none, nullptr));
+    CK(eng.gemm(P, ir, b, b, one, cv(Fc(LW), R0), OP_C, Fc(Gc), OP_N, one,
+                brv(F(S(w.gbar, i)), R0), zero, none, nullptr));
+    // LW = L W:  Lbar[:, C] += LWbar[:, R] W[C, R]^H,  Wbar[C, R] += L[:, C]^H LWbar[:, R]
+    CK(eng.gemm(P, b, ic, ir, one, cv(Fc(LWb), R0), OP_N, cv(Fc(Wm), R0), OP_C, one, F(Lbar),
+                zero, none, nullptr));
+    CK(eng.gemm(P, ic, ir, b, one, Fc(L), OP_C, cv(Fc(LWb), R0), OP_N, one, bcv(F(Wb), R0), zero,
+                none, nullptr));
+    // W = G_{i+1} t_i^H:  Gbar_{i+1} = Wbar t_i, nonzero on C x C only
+    if (ir < b || ic < b) CK(cudaMemsetAsync(Gn, 0, PB * sizeof(z64), s));
+    CK(eng.gemm(P, ic, ic, ir, one, cv(Fc(Wb), R0), OP_N, tv(Hu(i)), OP_N, zero, F(Gn), zero,
+                none, nullptr));
     std::swap(Gc, Gn);
     std::swap(GLc, GLn);
   }
@@ -410,17 +454,26 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
     z64* gb = S(w.gbar, i);
     z64* glb = S(w.glbar, i);
     if (i > 0) {
-      CK(eng.gemm(P, b, b, b, one, Fc(gF(i)), OP_N, Hu(i - 1), OP_C, zero, F(K), zero, none, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(glF(i - 1)), OP_N, Fc(K), OP_C, zero, F(Vt), zero, none, nullptr));
-      // g^<_i = K Vt (+ source)
-      CK(eng.gemm(P, b, b, b, one, Fc(glb), OP_N, Fc(Vt), OP_C, zero, F(Kb), zero, none, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(K), OP_C, Fc(glb), OP_N, zero, F(Vtb), zero, none, nullptr));
-      // Vt = g^<_{i-1} K^H
-      CK(eng.gemm(P, b, b, b, one, Fc(Vtb), OP_C, Fc(glF(i - 1)), OP_N, one, F(Kb), zero, none, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(Vtb), OP_N, Fc(K), OP_N, one, F(S(w.glbar, i - 1)), zero, none,
-                  nullptr));
-      // K = g_i t_{i-1}^H
-      CK(eng.gemm(P, b, b, b, one, Fc(Kb), OP_N, Hu(i - 1), OP_N, one, F(gb), zero, none, nullptr));
+      // K[:, R] = g_i[:, C] T^H;  Vt = g^<_{i-1}[:, R] K[:, R]^H
+      CK(eng.gemm(P, b, ir, ic, one, Fc(gF(i)), OP_N, tv(Hu(i - 1)), OP_C, zero, bcv(F(K), R0),
+                  zero, none, nullptr));
+      CK(eng.gemm(P, b, b, ir, one, cv(Fc(glF(i - 1)), R0), OP_N, cv(Fc(K), R0), OP_C, zero,
+                  F(Vt), zero, none, nullptr));
+      // g^<_i = K[:, R] Vt[R, :] (+ source):  Kbar[:, R] = g^<bar Vt[R, :]^H,
+      // Vtbar[R, :] = K[:, R]^H g^<bar
+      CK(eng.gemm(P, b, ir, b, one, Fc(glb), OP_N, rv(Fc(Vt), R0), OP_C, zero, bcv(F(Kb), R0),
+                  zero, none, nullptr));
+      CK(eng.gemm(P, ir, b, b, one, cv(Fc(K), R0), OP_C, Fc(glb), OP_N, zero, brv(F(Vtb), R0),
+                  zero, none, nullptr));
+      // Vt = g^<_{i-1}[:, R] K[:, R]^H:  Kbar[:, R] += Vtbar[R, :]^H g^<_{i-1}[R, R],
+      // g^<bar_{i-1}[R, R] += Vtbar[R, :] K[:, R]
+      CK(eng.gemm(P, b, ir, ir, one, rv(Fc(Vtb), R0), OP_C, rv(cv(Fc(glF(i - 1)), R0), R0), OP_N,
+                  one, bcv(F(Kb), R0), zero, none, nullptr));
+      CK(eng.gemm(P, ir, ir, b, one, rv(Fc(Vtb), R0), OP_N, cv(Fc(K), R0), OP_N, one,
+                  brv(bcv(F(S(w.glbar, i - 1)), R0), R0), zero, none, nullptr));
+      // K = g_i t_{i-1}^H:  gbar_i[:, C] += Kbar[:, R] T
+      CK(eng.gemm(P, b, ic, ir, one, cv(Fc(Kb), R0), OP_N, tv(Hu(i - 1)), OP_N, one, F(gb), zero,
+                  none, nullptr));
     }
     if (has_src(i)) {
       CK(build_src(i, Ssrc));
@@ -437,11 +490,12 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
     k_vbar<<<g2(b, P), kT, 0, s>>>(b, i, NB, Fc(Mb), w.vb);
     count_launch();
     if (i > 0) {
-      // M_i = ... - t^H L_{i-1}:  Lbar_{i-1} -= t Mbar;  L_{i-1} = g_{i-1} t
-      CK(eng.gemm(P, b, b, b, mone, Hu(i - 1), OP_N, Fc(Mb), OP_N, one, F(S(w.Lbar, i - 1)), zero,
-                  none, nullptr));
-      CK(eng.gemm(P, b, b, b, one, Fc(S(w.Lbar, i - 1)), OP_N, Hu(i - 1), OP_C, one,
-                  F(S(w.gbar, i - 1)), zero, none, nullptr));
+      // M_i = ... - Y with Y[C, C] = T^H L_{i-1}[R, C]:  Lbar_{i-1}[R, C] -= T Mbar[C, C];
+      // L_{i-1}[:, C] = g_{i-1}[:, R] T:  gbar_{i-1}[:, R] += Lbar[:, C] T^H
+      CK(eng.gemm(P, ir, ic, ic, mone, tv(Hu(i - 1)), OP_N, Fc(Mb), OP_N, one,
+                  brv(F(S(w.Lbar, i - 1)), R0), zero, none, nullptr));
+      CK(eng.gemm(P, b, ir, ic, one, Fc(S(w.Lbar, i - 1)), OP_N, tv(Hu(i - 1)), OP_C, one,
+                  bcv(F(S(w.gbar, i - 1)), R0), zero, none, nullptr));
     }
   }
 #undef RUN
@@ -492,6 +546,9 @@ extern "C" negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, c
       opt->adjoint_segment < 0 || opt->refine_max < 0 || opt->refine_max > 16)
     return NEGF_ERR_ARG;
   if (!sigma_valid(opt, dev->block)) return NEGF_ERR_ARG;
+  if (dev->iface_rows < 0 || dev->iface_rows > dev->block || dev->iface_cols < 0 ||
+      dev->iface_cols > dev->block)
+    return NEGF_ERR_ARG;
   if (!V_bar) return NEGF_ERR_ARG;
   const int b = dev->block, N = dev->n_slabs;
   const size_t NB = (size_t)N * b;
