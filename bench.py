@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--adj-slabs", type=int, default=20)
     ap.add_argument("--adj-segment", type=int, default=0,
                     help="--workload adjoint: slabs per checkpointed segment (0 = keep all)")
+    ap.add_argument("--adj-ckpt", action="store_true",
+                    help="--workload adjoint: time solve + adjoint with the solve's checkpoints "
+                         "handed to the adjoint, beside solve + a recomputing adjoint")
     ap.add_argument("--adj-iface", type=int, default=0,
                     help="--workload adjoint: hoppings supported on the last r rows / first r "
                          "columns (the facing atoms), r orbitals; 0 = dense")
@@ -321,8 +324,30 @@ def run_side(args):
         def adj():
             return negf.rgf_adjoint(D, Et, st, lead["sigma_R"], lead["sigma_L"], opt,
                                     density_bar=c, current_bar=d, V=Vt)
-        ms, _ = _timed(torch, adj, args.warmup, args.steps)
-        line.update(metric="adjoint points/s (forward sweep kept + reverse sweep, dL/dV)",
+        extra = {}
+        if args.adj_ckpt:
+            # the autograd step: solve + adjoint, with the solve's sweep blocks handed to the
+            # adjoint, against solve + an adjoint that recomputes them
+            ck = negf.checkpoint_buffer(D, 1)
+
+            def step_ck():
+                negf.rgf_solve(D, Et, st, lead["sigma_R"], lead["sigma_L"], opt, V=Vt,
+                               checkpoints=ck)
+                return negf.rgf_adjoint(D, Et, st, lead["sigma_R"], lead["sigma_L"], opt,
+                                        density_bar=c, current_bar=d, V=Vt, checkpoints=ck)
+
+            def step_re():
+                negf.rgf_solve(D, Et, st, lead["sigma_R"], lead["sigma_L"], opt, V=Vt)
+                return adj()
+            ms_re, _ = _timed(torch, step_re, args.warmup, args.steps)
+            ms, _ = _timed(torch, step_ck, args.warmup, args.steps)
+            extra = {"solve_plus_recomputing_adjoint_ms": ms_re / args.steps,
+                     "speedup_of_checkpoint_handoff": ms_re / ms}
+        else:
+            ms, _ = _timed(torch, adj, args.warmup, args.steps)
+        line.update(metric=("solve + adjoint points/s with the checkpoint hand-off (dL/dV)"
+                            if args.adj_ckpt else
+                            "adjoint points/s (forward sweep kept + reverse sweep, dL/dV)"),
                     value=args.steps / (ms / 1e3), unit="points/s", ms_per_step=ms / args.steps,
                     dtype="bf16-slices->fp32 (fp64 storage)",
                     config={"workload": f"adjoint, N={N} slabs x 3430 orbitals (343 atoms x 10),"
@@ -330,7 +355,7 @@ def run_side(args):
                                         + (f", hoppings on the {args.adj_iface} x "
                                            f"{args.adj_iface} facing-atom block"
                                            if args.adj_iface > 0 else ""),
-                            "adjoint_segment": args.adj_segment})
+                            "adjoint_segment": args.adj_segment, **extra})
     elif args.workload == "iface":
         # the benchmark device with interface couplings: every hopping block keeps only the
         # orbitals of the 10 facing atoms of each slab (its last 100 rows, first 100 columns)

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define NEGF_ABI_VERSION 3
+#define NEGF_ABI_VERSION 4
 
 typedef enum {
   NEGF_OK = 0,
@@ -179,6 +179,7 @@ const char* negf_status_string(negf_status s);
 #define NEGF_WS_LEAD 0
 #define NEGF_WS_RGF 1
 #define NEGF_WS_ADJOINT 2
+#define NEGF_WS_ADJOINT_CKPT 3 /* negf_rgf_adjoint given negf_rgf_solve's checkpoints */
 
 /* Bytes of device workspace a call of kind `which` needs for n_pts points (the library
  * works through the points `opt->chunk` at a time, so the size saturates). */
@@ -228,6 +229,9 @@ negf_status negf_lead_selfenergy(const negf_device* dev, int32_t n_pts, const do
  *   diagGR/GL   device complex128 [n_pts][N*b*A] out (nullable): diag G^R, diag G^< (A = 1)
  *               or their atom diagonal blocks (same layout as scat_R/L) for the
  *               self-consistent Born step (negf_scba_step, with n_orb = N b A)
+ *   checkpoints device, negf_checkpoint_bytes(dev, n_pts) bytes, out (nullable): the sweep
+ *               blocks negf_rgf_adjoint needs (forward g_i, g^<_i, L_i = g_i t_i; backward
+ *               G_ii, G^<_ii), so that it runs only its reverse passes
  *   Returns NEGF_ERR_ARG when sigma_structure is invalid or A does not divide b.
  *   status      device int32 [n_pts] out                                                 */
 negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* E,
@@ -236,8 +240,14 @@ negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* 
                            const int32_t* e_idx, int32_t n_rows, const negf_options* opt,
                            double* density,
                            double* current, double* transmission, double* diagGR,
-                           double* diagGL, int32_t* status, void* ws, size_t ws_bytes,
-                           void* stream);
+                           double* diagGL, void* checkpoints, int32_t* status, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/* Bytes of the sweep checkpoints of negf_rgf_solve for n_pts points: complex128
+ * [5][N][n_pts][b][b] (forward g, forward g^<, L, backward G, backward G^<, each slab-major with
+ * the points of a slab contiguous): 5 N b^2 complex numbers per point; 0 for an invalid
+ * device or n_pts < 1. */
+size_t negf_checkpoint_bytes(const negf_device* dev, int32_t n_pts);
 
 /* One self-consistent Born update of the phonon self-energies (Eqs. 4-6), entry by entry
  * (orbital diagonals, or every entry of the atom blocks with n_orb = N b A):
@@ -277,17 +287,22 @@ negf_status negf_scba_step_mesh(int32_t n_k, int32_t n_E, int32_t n_orb, const d
  * it accumulates V_bar[N][b] += sum_p sum_j density_bar[p][j] dn_j(p)/dV
  *                                 + sum_i current_bar[p][i] dj_i(p)/dV.
  * V_bar is device double [N][b] and is overwritten (not accumulated into).
- * Memory: every slab's forward and backward blocks are kept (8 N b^2 complex per point in
- * flight) unless opt->adjoint_segment = s with 0 < s < N: then only segment-boundary blocks are
- * kept and one segment at a time is recomputed (3 N + 5 s + 4 N / s blocks per point, about
- * 3 more forward sweeps and 1 more backward sweep); results agree to rounding.            */
+ * checkpoints (nullable): the blocks a negf_rgf_solve call wrote for the same device, points,
+ * V, self-energies and options (its `checkpoints` output); the adjoint then recomputes no sweep
+ * and keeps no sweep block of its own (workspace NEGF_WS_ADJOINT_CKPT: the cotangents, 3 N b^2
+ * complex per point, and temporaries).  Without them every slab's forward and backward blocks
+ * are recomputed and kept (8 N b^2 complex per point in flight, workspace NEGF_WS_ADJOINT)
+ * unless opt->adjoint_segment = s with 0 < s < N: then only segment-boundary blocks are kept
+ * and one segment at a time is recomputed (3 N + 5 s + 4 N / s blocks per point, about 3 more
+ * forward sweeps and 1 more backward sweep); results agree to rounding.                    */
 negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, const double* E,
                              const int32_t* sys_idx, const double* V, const double* sigma_R,
                              const double* sigma_L, const double* scat_R,
                              const double* scat_L, const int32_t* e_idx, int32_t n_rows,
-                             const negf_options* opt, const double* density_bar,
-                             const double* current_bar, double* V_bar, int32_t* status,
-                             void* ws, size_t ws_bytes, void* stream);
+                             const negf_options* opt, const void* checkpoints,
+                             const double* density_bar, const double* current_bar,
+                             double* V_bar, int32_t* status, void* ws, size_t ws_bytes,
+                             void* stream);
 
 /* Energy / k quadrature of Eqs. 7-8 in FP64 in a fixed order (deterministic):
  *   out[g][j] = sum over p with group[p] == g (in increasing p) of w[p] * in[p][j]

@@ -113,10 +113,13 @@ int adj_segment(const negf_options* opt, int N) {
   return (sg <= 0 || sg >= N) ? N : sg;
 }
 
-void carve_adj(char* base, size_t& off, int P, int b, int N, int seg, int prec, AdjWs& w) {
+void carve_adj(char* base, size_t& off, int P, int b, int N, int seg, int prec, bool ckpt,
+               AdjWs& w) {
   const size_t PB = (size_t)P * b * b;
   const size_t N1 = (size_t)std::max(N - 1, 1);
-  const size_t nseg = (size_t)((N + seg - 1) / seg);
+  // with the solve's checkpoints no sweep block is recomputed or kept here
+  const size_t nseg = ckpt ? 0 : (size_t)((N + seg - 1) / seg);
+  if (ckpt) seg = 0;
   w.sys = take<int32_t>(base, off, P);
   w.erow = take<int32_t>(base, off, P);
   w.gbar = take<z64>(base, off, N * PB);
@@ -164,6 +167,8 @@ struct AdjArgs {
   bool accumulate;
   int32_t* status;
   int A;  // scattering self-energy block width (1: orbital-diagonal)
+  const z64* ckpt;  // sweep checkpoints of negf_rgf_solve (nullable), [5][N][n_tot][b][b]
+  int n_tot, p0;    // points of the checkpoints; first point of this chunk
 };
 
 negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_t s) {
@@ -175,9 +180,14 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   const BMc<double> none{nullptr, 0, nullptr, 0};
   size_t off = 0;
   AdjWs w;
-  const int seg = adj_segment(a.opt, N);
+  const bool have_ck = a.ckpt != nullptr;
+  const int seg = have_ck ? N : adj_segment(a.opt, N);
   const int nseg = (N + seg - 1) / seg;
-  carve_adj(wsbase, off, P, b, N, seg, a.opt->precision, w);
+  carve_adj(wsbase, off, P, b, N, seg, a.opt->precision, have_ck, w);
+  // block of kind k of slab i in the solve's checkpoints (read only)
+  auto ck = [&](int k, int i) -> z64* {
+    return const_cast<z64*>(a.ckpt) + ckpt_offset(k, i, N, a.n_tot, a.p0, bb);
+  };
   Engine eng(s, a.opt->precision, a.opt->refine_steps, refine_limit(a.opt), w.eng, b,
              dev->n_sys);
   CK(eng.timeout_reset());
@@ -238,26 +248,34 @@ negf_status adjoint_chunk_run(const AdjArgs& a, int P, char* wsbase, cudaStream_
   };
   const double eta = a.opt->eta_device;
 
-  // ---- segment bookkeeping: which segment's forward / backward blocks are resident
-  int resF = -1, resB = -1;
+  // ---- segment bookkeeping: which segment's forward / backward blocks are resident (with the
+  // solve's checkpoints every block of the one segment is, and nothing is recomputed)
+  int resF = have_ck ? 0 : -1, resB = have_ck ? 0 : -1;
   auto seg_lo = [&](int c) { return c * seg; };
   auto seg_hi = [&](int c) { return std::min(N, (c + 1) * seg); };
   // forward blocks of slab i: the resident segment, or the checkpoint just below it
   auto gF = [&](int i) -> z64* {
+    if (have_ck) return ck(CK_G_FWD, i);
     if (i >= seg_lo(resF) && i < seg_hi(resF)) return S(w.sg, i - seg_lo(resF));
     return S(w.ckg, resF);  // i == seg_lo(resF) - 1
   };
   auto glF = [&](int i) -> z64* {
+    if (have_ck) return ck(CK_GL_FWD, i);
     if (i >= seg_lo(resF) && i < seg_hi(resF)) return S(w.sgl, i - seg_lo(resF));
     return S(w.ckgl, resF);
   };
-  auto Lb = [&](int i) -> z64* { return S(w.sL, i - seg_lo(resF)); };
+  auto Lb = [&](int i) -> z64* {
+    if (have_ck) return ck(CK_L, i);
+    return S(w.sL, i - seg_lo(resF));
+  };
   // backward blocks of slab i: the resident segment, or the checkpoint just above it
   auto Gb = [&](int i) -> z64* {
+    if (have_ck) return ck(CK_G, i);
     if (i >= seg_lo(resB) && i < seg_hi(resB)) return S(w.sG, i - seg_lo(resB));
     return S(w.ckG, resB);  // i == seg_hi(resB)
   };
   auto GLb = [&](int i) -> z64* {
+    if (have_ck) return ck(CK_GL, i);
     if (i >= seg_lo(resB) && i < seg_hi(resB)) return S(w.sGL, i - seg_lo(resB));
     return S(w.ckGL, resB);
   };
@@ -510,17 +528,17 @@ constexpr size_t kAdjBudget = 32ull << 30;
 
 }  // namespace
 
-size_t adjoint_bytes(const negf_device* dev, int P, const negf_options* opt) {
+size_t adjoint_bytes(const negf_device* dev, int P, const negf_options* opt, bool ckpt) {
   size_t off = 0;
   AdjWs w;
   carve_adj(nullptr, off, P, dev->block, dev->n_slabs, adj_segment(opt, dev->n_slabs),
-            opt->precision, w);
+            opt->precision, ckpt, w);
   return off + 256;
 }
 
-int adjoint_chunk(const negf_device* dev, int n_pts, const negf_options* opt) {
+int adjoint_chunk(const negf_device* dev, int n_pts, const negf_options* opt, bool ckpt) {
   if (opt->chunk > 0) return std::max(1, std::min(std::min(opt->chunk, n_pts), 16384));
-  const size_t per = adjoint_bytes(dev, 2, opt) - adjoint_bytes(dev, 1, opt);
+  const size_t per = adjoint_bytes(dev, 2, opt, ckpt) - adjoint_bytes(dev, 1, opt, ckpt);
   size_t c = std::max<size_t>(1, kAdjBudget / std::max<size_t>(per, 1));
   return (int)std::max<size_t>(1, std::min<size_t>(c, (size_t)std::max(n_pts, 1)));
 }
@@ -534,10 +552,10 @@ extern "C" negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, c
                                         const double* sigma_R, const double* sigma_L,
                                         const double* scat_R, const double* scat_L,
                                         const int32_t* e_idx, int32_t n_rows,
-                                        const negf_options* opt, const double* density_bar,
-                                        const double* current_bar, double* V_bar,
-                                        int32_t* status, void* ws, size_t ws_bytes,
-                                        void* stream) {
+                                        const negf_options* opt, const void* checkpoints,
+                                        const double* density_bar, const double* current_bar,
+                                        double* V_bar, int32_t* status, void* ws,
+                                        size_t ws_bytes, void* stream) {
   if (!dev || !opt || dev->n_sys < 1 || dev->n_slabs < 1 || dev->block < 1 || !dev->H_diag ||
       (dev->n_slabs > 1 && !dev->H_up) || n_pts < 0)
     return NEGF_ERR_ARG;
@@ -560,8 +578,9 @@ extern "C" negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, c
   if (!E || !sys_idx || !sigma_R || !sigma_L || !status) return NEGF_ERR_ARG;
   if ((scat_R == nullptr) != (scat_L == nullptr)) return NEGF_ERR_ARG;
   if (scat_R && (e_idx ? n_rows < 1 : n_rows < n_pts)) return NEGF_ERR_ARG;
-  const int C = adjoint_chunk(dev, n_pts, opt);
-  if (!ws || ws_bytes < adjoint_bytes(dev, C, opt)) return NEGF_ERR_NOMEM;
+  const bool ckpt = checkpoints != nullptr;
+  const int C = adjoint_chunk(dev, n_pts, opt, ckpt);
+  if (!ws || ws_bytes < adjoint_bytes(dev, C, opt, ckpt)) return NEGF_ERR_NOMEM;
   if (cudaMemsetAsync(status, 0, (size_t)n_pts * sizeof(int32_t), s) != cudaSuccess)
     return NEGF_ERR_CUDA;
   const size_t bb = (size_t)b * b;
@@ -581,6 +600,9 @@ extern "C" negf_status negf_rgf_adjoint(const negf_device* dev, int32_t n_pts, c
     a.scatL = scat_L ? reinterpret_cast<const z64*>(scat_L) + (e_idx ? 0 : (size_t)p0 * NB * A)
                      : nullptr;
     a.A = A;
+    a.ckpt = static_cast<const z64*>(checkpoints);
+    a.n_tot = n_pts;
+    a.p0 = p0;
     a.opt = opt;
     a.nbar = density_bar ? density_bar + (size_t)p0 * NB : nullptr;
     a.jbar = (current_bar && N > 1) ? current_bar + (size_t)p0 * (N - 1) : nullptr;

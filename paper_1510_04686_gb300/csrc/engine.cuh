@@ -105,7 +105,15 @@ void engine_fail_waits(int on);
 bool engine_supports(int precision, int b);
 
 // Adjoint workspace helpers (adjoint.cu)
-size_t adjoint_bytes(const negf_device* dev, int P, const negf_options* opt);
-int adjoint_chunk(const negf_device* dev, int n_pts, const negf_options* opt);
+// ckpt: the sweep blocks come from negf_rgf_solve's checkpoints (no resident segment blocks)
+size_t adjoint_bytes(const negf_device* dev, int P, const negf_options* opt, bool ckpt);
+int adjoint_chunk(const negf_device* dev, int n_pts, const negf_options* opt, bool ckpt);
+// Sweep checkpoints handed from negf_rgf_solve to negf_rgf_adjoint: complex128
+// [5][N][n_pts][b][b], the kinds below, slab-major so that a chunk of consecutive points of one
+// slab is contiguous (item stride b^2).
+enum CkptKind { CK_G_FWD = 0, CK_GL_FWD = 1, CK_L = 2, CK_G = 3, CK_GL = 4, CK_KINDS = 5 };
+inline size_t ckpt_offset(int kind, int slab, int N, int n_pts, int p, size_t bb) {
+  return ((size_t)(kind * N + slab) * (size_t)n_pts + (size_t)p) * bb;
+}
 
 }  // namespace negf

@@ -323,6 +323,8 @@ struct RgfArgs {
   z64* dGL;
   int A;  // scattering self-energy block width (1: orbital-diagonal)
   int32_t* status;
+  z64* ckpt;  // sweep checkpoints for negf_rgf_adjoint (nullable), [5][N][n_tot][b][b]
+  int n_tot, p0;
 };
 
 negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s) {
@@ -429,6 +431,17 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
     }
   }
 
+  // ---- checkpoints of the forward sweep (g_i, g^<_i are overwritten by the backward sweep)
+  const size_t blk = (size_t)P * bb * sizeof(z64);
+  auto ckp = [&](int k, int i) { return a.ckpt + ckpt_offset(k, i, N, a.n_tot, a.p0, bb); };
+  if (a.ckpt) {
+    for (int i = 0; i < N; ++i) {
+      CK(cudaMemcpyAsync(ckp(CK_G_FWD, i), G[i], blk, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(ckp(CK_GL_FWD, i), GL[i], blk, cudaMemcpyDeviceToDevice, s));
+      if (i + 1 < N) CK(cudaMemcpyAsync(ckp(CK_L, i), Lb(i), blk, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+
   // ---- transmission from G_NN = g_N and Gamma_R
   if (a.transmission) {
     CK(launch_gamma(s, P, b, SigR_R, F(w.S), nullptr));
@@ -471,6 +484,12 @@ negf_status rgf_chunk_run(const RgfArgs& a, int P, char* wsbase, cudaStream_t s)
     std::swap(G[i], spare);
     CK(launch_slab_obs(s, P, b, i, NB, a.A, Fc(G[i]), Fc(GL[i]), a.density, a.dGR, a.dGL,
                        nullptr));
+  }
+  if (a.ckpt) {
+    for (int i = 0; i < N; ++i) {
+      CK(cudaMemcpyAsync(ckp(CK_G, i), G[i], blk, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(ckp(CK_GL, i), GL[i], blk, cudaMemcpyDeviceToDevice, s));
+    }
   }
   if (a.density) CK(launch_check_finite(s, a.density, NB, P, a.status));
   if (a.current && N > 1) CK(launch_check_finite(s, a.current, N - 1, P, a.status));
@@ -536,9 +555,18 @@ size_t negf_workspace_size(const negf_device* dev, int32_t n_pts, const negf_opt
   switch (which) {
     case NEGF_WS_LEAD: return lead_bytes(lead_chunk(dev, n_pts, opt), b, opt);
     case NEGF_WS_RGF: return rgf_bytes(rgf_chunk(dev, n_pts, opt), b, N, opt);
-    case NEGF_WS_ADJOINT: return adjoint_bytes(dev, adjoint_chunk(dev, n_pts, opt), opt);
+    case NEGF_WS_ADJOINT:
+      return adjoint_bytes(dev, adjoint_chunk(dev, n_pts, opt, false), opt, false);
+    case NEGF_WS_ADJOINT_CKPT:
+      return adjoint_bytes(dev, adjoint_chunk(dev, n_pts, opt, true), opt, true);
   }
   return 0;
+}
+
+size_t negf_checkpoint_bytes(const negf_device* dev, int32_t n_pts) {
+  if (!valid_dev(dev) || n_pts < 1) return 0;
+  const size_t bb = (size_t)dev->block * dev->block;
+  return ckpt_offset(CK_KINDS, 0, dev->n_slabs, n_pts, 0, bb) * sizeof(z64);
 }
 
 negf_status negf_lead_selfenergy(const negf_device* dev, int32_t n_pts, const double* E,
@@ -573,8 +601,8 @@ negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* 
                            const double* sigma_L, const double* scat_R, const double* scat_L,
                            const int32_t* e_idx, int32_t n_rows, const negf_options* opt,
                            double* density, double* current, double* transmission,
-                           double* diagGR, double* diagGL, int32_t* status, void* ws,
-                           size_t ws_bytes, void* stream) {
+                           double* diagGR, double* diagGL, void* checkpoints, int32_t* status,
+                           void* ws, size_t ws_bytes, void* stream) {
   if (!valid_dev(dev) || !valid_opt(opt) || n_pts < 0) return NEGF_ERR_ARG;
   if (scat_R && (e_idx ? n_rows < 1 : n_rows < n_pts)) return NEGF_ERR_ARG;
   if (!sigma_valid(opt, dev->block)) return NEGF_ERR_ARG;
@@ -612,6 +640,9 @@ negf_status negf_rgf_solve(const negf_device* dev, int32_t n_pts, const double* 
     a.dGR = diagGR ? reinterpret_cast<z64*>(diagGR) + (size_t)p0 * NBA : nullptr;
     a.dGL = diagGL ? reinterpret_cast<z64*>(diagGL) + (size_t)p0 * NBA : nullptr;
     a.A = A;
+    a.ckpt = static_cast<z64*>(checkpoints);
+    a.n_tot = n_pts;
+    a.p0 = p0;
     a.status = status + p0;
     negf_status r = rgf_chunk_run(a, P, static_cast<char*>(ws), s);
     if (r != NEGF_OK) return r;

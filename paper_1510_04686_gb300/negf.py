@@ -21,7 +21,7 @@ PREC_MIXED_56 = 3    # tensor cores, 56-bit operand values
 PREC_AUTO = -1       # lead_precision: FP64 for the FP64 form, else 56-bit (48 beyond b = 7008)
 SIGMA_ORBITAL_DIAG = 0  # scattering self-energies: one value per orbital
 SIGMA_ATOM_BLOCK = 1    # scattering self-energies: one atom_orbitals^2 block per atom
-WS_LEAD, WS_RGF, WS_ADJOINT = 0, 1, 2
+WS_LEAD, WS_RGF, WS_ADJOINT, WS_ADJOINT_CKPT = 0, 1, 2, 3
 
 _STATUS = {
     0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "workspace too small",
@@ -67,7 +67,8 @@ EXPORTS = ("negf_default_options", "negf_abi_version", "negf_status_string",
            "negf_launch_count", "negf_zinv_batched_noalloc", "negf_tc_config_count",
            "negf_tc_config_set", "negf_tc_config_get", "negf_last_cuda_error",
            "negf_fp64_fallback_count", "negf_debug_fail_waits", "negf_poisson_apply",
-           "negf_orbitals_to_atoms", "negf_atoms_to_orbitals", "negf_scba_step_mesh")
+           "negf_orbitals_to_atoms", "negf_atoms_to_orbitals", "negf_scba_step_mesh",
+           "negf_checkpoint_bytes")
 
 
 def library():
@@ -92,13 +93,15 @@ def library():
                                          P, c_size_t, P]
     lib.negf_lead_selfenergy.restype = c_int32
     lib.negf_rgf_solve.argtypes = [POINTER(_Dev), c_int32, P, P, P, P, P, P, P, P, c_int32,
-                                   POINTER(_Opt), P, P, P, P, P, P, P, c_size_t, P]
+                                   POINTER(_Opt), P, P, P, P, P, P, P, P, c_size_t, P]
     lib.negf_rgf_solve.restype = c_int32
     lib.negf_scba_step.argtypes = [c_int32, c_int32, c_int32, P, c_double, c_double, c_int32,
                                    c_double, c_double, P, P, P, P, P, P]
     lib.negf_scba_step.restype = c_int32
     lib.negf_rgf_adjoint.argtypes = [POINTER(_Dev), c_int32, P, P, P, P, P, P, P, P, c_int32,
-                                     POINTER(_Opt), P, P, P, P, P, c_size_t, P]
+                                     POINTER(_Opt), P, P, P, P, P, P, c_size_t, P]
+    lib.negf_checkpoint_bytes.argtypes = [POINTER(_Dev), c_int32]
+    lib.negf_checkpoint_bytes.restype = c_size_t
     lib.negf_rgf_adjoint.restype = c_int32
     lib.negf_integrate.argtypes = [c_int32, c_int32, c_int32, P, P, P, P, P]
     lib.negf_integrate.restype = c_int32
@@ -255,9 +258,23 @@ def lead_selfenergy(dev: Device, E: torch.Tensor, sys_idx: torch.Tensor, opt: _O
     return dict(sigma_R=sR, sigma_L=sL, iters=it, status=st)
 
 
+def checkpoint_buffer(dev: Device, n_pts: int, device=None):
+    """A buffer for the sweep checkpoints negf_rgf_solve hands to negf_rgf_adjoint:
+    complex128 [5, N, n_pts, b, b] (5 N b^2 complex numbers per point)."""
+    nb = int(library().negf_checkpoint_bytes(ctypes.byref(dev.c), int(n_pts)))
+    if nb == 0:
+        raise ValueError("no checkpoints for this device / point count")
+    return torch.empty((5, dev.N, n_pts, dev.b, dev.b), dtype=torch.complex128,
+                       device=device if device is not None else dev.H_diag.device)
+
+
 def rgf_solve(dev: Device, E, sys_idx, sigma_R, sigma_L, opt, V=None, scat_R=None, scat_L=None,
-              e_idx=None, outputs=("density", "current", "transmission"), diag=False):
-    """Forward/backward RGF sweeps and observables for every point (negf_rgf_solve)."""
+              e_idx=None, outputs=("density", "current", "transmission"), diag=False,
+              checkpoints=None):
+    """Forward/backward RGF sweeps and observables for every point (negf_rgf_solve).
+
+    checkpoints: an optional buffer from checkpoint_buffer(dev, n) that receives the sweep blocks
+    for a later rgf_adjoint of the same points."""
     _need(E, torch.float64, "E")
     n = E.numel()
     N, b = dev.N, dev.b
@@ -274,6 +291,8 @@ def rgf_solve(dev: Device, E, sys_idx, sigma_R, sigma_L, opt, V=None, scat_R=Non
             raise ValueError(f"scat_R rows must hold N*b*{A} entries")
     if e_idx is not None:
         _need(e_idx, torch.int32, "e_idx", (n,))
+    if checkpoints is not None:
+        _need(checkpoints, torch.complex128, "checkpoints", (5, N, n, b, b))
     dv = E.device
     out = {}
     dens = torch.empty((n, N * b), dtype=torch.float64, device=dv) if "density" in outputs else None
@@ -289,8 +308,8 @@ def rgf_solve(dev: Device, E, sys_idx, sigma_R, sigma_L, opt, V=None, scat_R=Non
                                     _ptr(sigma_R), _ptr(sigma_L), _ptr(scat_R), _ptr(scat_L),
                                     _ptr(e_idx), _rows(scat_R), ctypes.byref(opt), _ptr(dens),
                                     _ptr(cur),
-                                    _ptr(tr), _ptr(dGR), _ptr(dGL), _ptr(st), _ptr(ws), nb,
-                                    _stream()), "negf_rgf_solve")
+                                    _ptr(tr), _ptr(dGR), _ptr(dGL), _ptr(checkpoints), _ptr(st),
+                                    _ptr(ws), nb, _stream()), "negf_rgf_solve")
     out.update(density=dens, current=cur, transmission=tr, diagGR=dGR, diagGL=dGL, status=st)
     return out
 
@@ -334,8 +353,12 @@ def scba_step_mesh(diagGR, diagGL, w_k, E, sigma_R, sigma_L, D_ac, D_op, hw, n0,
 
 
 def rgf_adjoint(dev: Device, E, sys_idx, sigma_R, sigma_L, opt, density_bar=None,
-                current_bar=None, V=None, scat_R=None, scat_L=None, e_idx=None):
-    """dL/dV for cotangents of density [n, N*b] and current [n, N-1] (negf_rgf_adjoint)."""
+                current_bar=None, V=None, scat_R=None, scat_L=None, e_idx=None,
+                checkpoints=None):
+    """dL/dV for cotangents of density [n, N*b] and current [n, N-1] (negf_rgf_adjoint).
+
+    checkpoints: the buffer an rgf_solve of the same points, V and options filled; the sweeps
+    are then not recomputed."""
     _need(E, torch.float64, "E")
     n = E.numel()
     N, b = dev.N, dev.b
@@ -347,15 +370,17 @@ def rgf_adjoint(dev: Device, E, sys_idx, sigma_R, sigma_L, opt, density_bar=None
         _need(V, torch.float64, "V", (N, b))
     if scat_R is not None and scat_R.shape[-1] != N * b * sigma_width(opt):
         raise ValueError(f"scat_R rows must hold N*b*{sigma_width(opt)} entries")
+    if checkpoints is not None:
+        _need(checkpoints, torch.complex128, "checkpoints", (5, N, n, b, b))
     dv = E.device
     Vbar = torch.empty((N, b), dtype=torch.float64, device=dv)
     st = torch.empty((n,), dtype=torch.int32, device=dv)
-    nb = workspace_size(dev, max(n, 1), opt, WS_ADJOINT)
+    nb = workspace_size(dev, max(n, 1), opt, WS_ADJOINT if checkpoints is None else WS_ADJOINT_CKPT)
     ws = _workspace(nb, dv)
     _check(library().negf_rgf_adjoint(ctypes.byref(dev.c), n, _ptr(E), _ptr(sys_idx), _ptr(V),
                                       _ptr(sigma_R), _ptr(sigma_L), _ptr(scat_R), _ptr(scat_L),
                                       _ptr(e_idx), _rows(scat_R), ctypes.byref(opt),
-                                      _ptr(density_bar),
+                                      _ptr(checkpoints), _ptr(density_bar),
                                       _ptr(current_bar), _ptr(Vbar), _ptr(st), _ptr(ws), nb,
                                       _stream()), "negf_rgf_adjoint")
     return Vbar, st
@@ -459,32 +484,39 @@ class RGFFunction(torch.autograd.Function):
 
     Forward runs negf_rgf_solve; backward runs negf_rgf_adjoint with the incoming cotangents, so
     autograd returns dL/dV for any scalar L built from the density and current (the gradient a
-    Newton-Poisson loop needs).  Lead and scattering self-energies are held fixed."""
+    Newton-Poisson loop needs).  Lead and scattering self-energies are held fixed.  With
+    keep_sweeps the forward pass keeps the sweep checkpoints (5 N b^2 complex per point) and the
+    backward pass recomputes no sweep."""
 
     @staticmethod
     def forward(ctx, V, dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R=None, scat_L=None,
-                e_idx=None):
+                e_idx=None, keep_sweeps=False):
+        ck = checkpoint_buffer(dev, E.numel(), E.device) if keep_sweeps else None
         out = rgf_solve(dev, E, sys_idx, sigma_R, sigma_L, opt, V=V.detach().contiguous(),
                         scat_R=scat_R, scat_L=scat_L, e_idx=e_idx,
-                        outputs=("density", "current"))
-        ctx.args = (dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R, scat_L, e_idx)
+                        outputs=("density", "current"), checkpoints=ck)
+        ctx.args = (dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R, scat_L, e_idx, ck)
         ctx.save_for_backward(V.detach())
         return out["density"], out["current"]
 
     @staticmethod
     def backward(ctx, g_density, g_current):
         (V,) = ctx.saved_tensors
-        dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R, scat_L, e_idx = ctx.args
+        dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R, scat_L, e_idx, ck = ctx.args
         gd = None if g_density is None else g_density.contiguous()
         gc = None if g_current is None else g_current.contiguous()
         Vbar, _ = rgf_adjoint(dev, E, sys_idx, sigma_R, sigma_L, opt, density_bar=gd,
-                              current_bar=gc, V=V, scat_R=scat_R, scat_L=scat_L, e_idx=e_idx)
-        return (Vbar,) + (None,) * 9
+                              current_bar=gc, V=V, scat_R=scat_R, scat_L=scat_L, e_idx=e_idx,
+                              checkpoints=ck)
+        return (Vbar,) + (None,) * 10
 
 
-def rgf(V, dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R=None, scat_L=None, e_idx=None):
-    """Differentiable (density, current) of the points with respect to V."""
-    return RGFFunction.apply(V, dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R, scat_L, e_idx)
+def rgf(V, dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R=None, scat_L=None, e_idx=None,
+        keep_sweeps=False):
+    """Differentiable (density, current) of the points with respect to V; keep_sweeps hands the
+    solve's sweep blocks to the adjoint instead of recomputing them."""
+    return RGFFunction.apply(V, dev, E, sys_idx, sigma_R, sigma_L, opt, scat_R, scat_L, e_idx,
+                             keep_sweeps)
 
 
 def tc_config(idx=None):
@@ -706,7 +738,8 @@ def atoms_to_orbitals(U, b, per=ORBITALS_PER_ATOM):
 
 
 def poisson_newton(dev: Device, E, w, sys_idx, opt: _Opt, n_D, kappa, c_x, c_y, U_L=0.0,
-                   U_R=0.0, U0=None, tol=1e-9, max_iter=30, per=ORBITALS_PER_ATOM):
+                   U_R=0.0, U0=None, tol=1e-9, max_iter=30, per=ORBITALS_PER_ATOM,
+                   keep_sweeps=True):
     """Self-consistent NEGF-Poisson solution (Eqs. 1, 7 and 9): Newton's method on
     F(U) = K U - boundary terms - kappa (n(U) - n_D) = 0 for the potential energy U [N, A] per
     atom, the electrons per atom n(U) = sum_p w[p] n(E_p, U) summed over each atom's orbitals.
@@ -716,7 +749,9 @@ def poisson_newton(dev: Device, E, w, sys_idx, opt: _Opt, n_D, kappa, c_x, c_y, 
     J = K - kappa dn/dU, whose row for atom a is one adjoint sweep (negf_rgf_adjoint, the
     backward of RGFFunction) with the cotangent w[p] on atom a's orbitals; the Newton step is
     J^-1 (-F) by the FP64 block inverse and GEMM.  Lead self-energies do not depend on U and
-    are computed once.  Returns (U, list of max |F| per iteration)."""
+    are computed once.  With keep_sweeps (5 N b^2 complex per point) the step's solve hands its
+    sweep blocks to every adjoint sweep of the step, which then run only their reverse passes.
+    Returns (U, list of max |F| per iteration)."""
     N, b = dev.N, dev.b
     A = -(-b // per)
     n_pts = E.numel()
@@ -735,10 +770,12 @@ def poisson_newton(dev: Device, E, w, sys_idx, opt: _Opt, n_D, kappa, c_x, c_y, 
         unit.view(-1)[j] = 0.0
     hist = []
     cot = torch.zeros((n_pts, N * b), dtype=torch.float64, device=dv)
+    # the sweep blocks of each Newton step's solve serve all of its adjoint sweeps
+    ck = checkpoint_buffer(dev, n_pts, dv) if keep_sweeps else None
     for _ in range(max_iter):
         V = atoms_to_orbitals(U, b, per)
         out = rgf_solve(dev, E, sys_idx, lead["sigma_R"], lead["sigma_L"], opt, V=V,
-                        outputs=("density",))
+                        outputs=("density",), checkpoints=ck)
         n = orbitals_to_atoms(integrate(out["density"], w), N, b, per)[0]
         F = poisson_apply(U, c_x, c_y, U_L, U_R, kappa, n, n_D)
         hist.append(float(F.abs().max().item()))
@@ -750,7 +787,7 @@ def poisson_newton(dev: Device, E, w, sys_idx, opt: _Opt, n_D, kappa, c_x, c_y, 
                 lo, hi = i * b + per * a, i * b + min(per * a + per, b)
                 cot[:, lo:hi] = w[:, None]
                 Vbar, _ = rgf_adjoint(dev, E, sys_idx, lead["sigma_R"], lead["sigma_L"], opt,
-                                      density_bar=cot, V=V)
+                                      density_bar=cot, V=V, checkpoints=ck)
                 cot[:, lo:hi] = 0.0
                 chi[i * A + a] = orbitals_to_atoms(Vbar, N, b, per).view(-1)
         # J = K - kappa chi  (as complex128 for the block kernels); delta = -J^-1 F

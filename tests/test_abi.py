@@ -37,7 +37,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_defaults_and_strings(lib):
-    assert lib.negf_abi_version() == 3
+    assert lib.negf_abi_version() == 4
     o = negf.options()
     assert o.eta_lead == 1e-6 and o.eta_device == 1e-6 and o.sr_max_iter == 100
     assert o.precision == negf.PREC_FP64 and o.refine_steps == 2
@@ -75,16 +75,18 @@ def test_bad_arguments_rejected_on_host(lib):
     d = _dev()
     # missing H_up with N > 1
     r = lib.negf_rgf_solve(ctypes.byref(_dev(hu=0)), 3, fake, fake, None, fake, fake, None, None,
-                           None, 0, ctypes.byref(o), None, None, None, None, None, fake, fake, 1 << 30,
-                           None)
+                           None, 0, ctypes.byref(o), None, None, None, None, None, None, fake, fake,
+                           1 << 30, None)
     assert r == 1
     # scat_R without scat_L
     r = lib.negf_rgf_solve(ctypes.byref(d), 3, fake, fake, None, fake, fake, fake, None, None,
-                           1, ctypes.byref(o), None, None, None, None, None, fake, fake, 1 << 30, None)
+                           1, ctypes.byref(o), None, None, None, None, None, None, fake, fake, 1 << 30,
+                           None)
     assert r == 1
     # workspace too small
     r = lib.negf_rgf_solve(ctypes.byref(d), 3, fake, fake, None, fake, fake, None, None, None,
-                           0, ctypes.byref(o), None, None, None, None, None, fake, fake, 16, None)
+                           0, ctypes.byref(o), None, None, None, None, None, None, fake, fake, 16,
+                           None)
     assert r == 3
     # bad options
     bad = negf.options(kT=0.0)
@@ -99,7 +101,8 @@ def test_bad_arguments_rejected_on_host(lib):
     assert r == 1
     # zero points is a no-op
     r = lib.negf_rgf_solve(ctypes.byref(d), 0, None, None, None, None, None, None, None, None,
-                           0, ctypes.byref(o), None, None, None, None, None, None, None, 0, None)
+                           0, ctypes.byref(o), None, None, None, None, None, None, None, None, 0,
+                           None)
     assert r == 0
 
 
@@ -159,8 +162,8 @@ def test_mixed_form_rejects_contractions_beyond_its_exact_range(lib):
     o_mixed = negf.options(precision=mixed)
     assert lib.negf_workspace_size(ctypes.byref(big), 1, ctypes.byref(o_mixed), B.WS_RGF) == 0
     r = lib.negf_rgf_solve(ctypes.byref(big), 1, fake, fake, None, fake, fake, None, None, None,
-                           0, ctypes.byref(o_mixed), None, None, None, None, None, fake, fake,
-                           1 << 40, None)
+                           0, ctypes.byref(o_mixed), None, None, None, None, None, None, fake,
+                           fake, 1 << 40, None)
     assert r == 8
     r = lib.negf_lead_selfenergy(ctypes.byref(big), 1, fake, fake, ctypes.byref(o_mixed), fake,
                                  fake, None, fake, fake, 1 << 40, None)
@@ -244,10 +247,23 @@ def test_sigma_structure_is_validated(lib):
         if ok:
             continue
         r = lib.negf_rgf_solve(ctypes.byref(d), 1, fake, fake, None, fake, fake, None, None,
-                               None, 0, ctypes.byref(o), None, None, None, None, None, fake,
-                               fake, 1 << 40, None)
+                               None, 0, ctypes.byref(o), None, None, None, None, None, None,
+                               fake, fake, 1 << 40, None)
         assert r == 1, A
         r = lib.negf_rgf_adjoint(ctypes.byref(d), 1, fake, fake, None, fake, fake, None, None,
-                                 None, 0, ctypes.byref(o), None, None, fake, fake, fake, 1 << 40,
-                                 None)
+                                 None, 0, ctypes.byref(o), None, None, None, fake, fake, fake,
+                                 1 << 40, None)
         assert r == 1, A
+
+
+def test_checkpoint_sizes(lib):
+    """negf_rgf_solve's checkpoints hold 5 N b^2 complex numbers per point, and the adjoint that
+    reads them needs a smaller workspace than the one that recomputes the sweeps."""
+    d = _dev(N=6, b=40)
+    o = negf.options()
+    assert lib.negf_checkpoint_bytes(ctypes.byref(d), 3) == 5 * 6 * 3 * 40 * 40 * 16
+    assert lib.negf_checkpoint_bytes(ctypes.byref(d), 0) == 0
+    assert lib.negf_checkpoint_bytes(ctypes.byref(_dev(N=0)), 3) == 0
+    full = lib.negf_workspace_size(ctypes.byref(d), 3, ctypes.byref(o), B.WS_ADJOINT)
+    ck = lib.negf_workspace_size(ctypes.byref(d), 3, ctypes.byref(o), B.WS_ADJOINT_CKPT)
+    assert 0 < ck < full

@@ -175,3 +175,39 @@ def test_adjoint_finite_differences_on_16_atoms():
         fd = (loss(Vp) - loss(Vm)) / (2 * h)
         ga = g[i, sl].sum()
         assert abs(fd - ga) <= 1e-5 * max(abs(ga), 1e-3 * np.abs(g).max()), (i, a, fd, ga)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("scatter,chunk", [(False, 0), (True, 0), (True, 2)])
+def test_adjoint_from_solve_checkpoints(prec, scatter, chunk):
+    """negf_rgf_solve's checkpoints hand the sweep blocks to negf_rgf_adjoint: the same V_bar as
+    the adjoint that recomputes them (same arithmetic, so to rounding), also when the solve and
+    the adjoint split the points into different chunks."""
+    N, b = 6, 20
+    dev, E, V, c, d, sR, sL = _setup(N, b, 77, 5, scatter=scatter)
+    opt = negf.options(precision=prec)
+    g_ref, (D, Et, st, lead, kw) = _gpu_grad(dev, E, V, c, d, opt, sR, sL)
+    ck = negf.checkpoint_buffer(D, len(E))
+    Vt = torch.as_tensor(V, device="cuda")
+    negf.rgf_solve(D, Et, st, lead["sigma_R"], lead["sigma_L"], negf.options(precision=prec),
+                   V=Vt, checkpoints=ck, **kw)
+    g, status = negf.rgf_adjoint(D, Et, st, lead["sigma_R"], lead["sigma_L"],
+                                 negf.options(precision=prec, chunk=chunk),
+                                 density_bar=torch.as_tensor(c, device="cuda"),
+                                 current_bar=torch.as_tensor(d, device="cuda"), V=Vt,
+                                 checkpoints=ck, **kw)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    assert np.abs(g.cpu().numpy() - g_ref).max() <= 1e-12 * np.abs(g_ref).max()
+
+
+def test_autograd_keeps_the_sweeps():
+    dev, E, V, c, d, sR, sL = _setup(4, 6, 13, 3)
+    opt = negf.options()
+    g_ref, (D, Et, st, lead, kw) = _gpu_grad(dev, E, V, c, d, opt)
+    Vt = torch.as_tensor(V, device="cuda").requires_grad_(True)
+    dens, cur = negf.rgf(Vt, D, Et, st, lead["sigma_R"], lead["sigma_L"], opt, keep_sweeps=True)
+    loss = (torch.as_tensor(c, device="cuda") * dens).sum() + \
+        (torch.as_tensor(d, device="cuda") * cur).sum()
+    loss.backward()
+    assert np.abs(Vt.grad.cpu().numpy() - g_ref).max() <= 1e-12 * np.abs(g_ref).max()

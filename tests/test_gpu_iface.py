@@ -128,3 +128,27 @@ def test_interface_adjoint_matches_dense_and_oracle(prec, seg, N, b, r, c):
         assert np.abs(g - ref).max() <= tol * scale
     if prec == 0:  # same nonzero terms, summed in another order
         assert np.abs(grads["sparse"] - grads["dense"]).max() <= 1e-10 * scale
+
+
+def test_interface_adjoint_from_solve_checkpoints():
+    N, b, r, c = 5, 40, 10, 20
+    dev = make_device(N, b, 2222, ge_frac=0.1, iface=(r, c))
+    rng = np.random.default_rng(3)
+    E = np.array([-0.9, 0.15, 1.1])
+    V = _t(rng.uniform(-0.2, 0.2, (N, b)))
+    cb, db = _t(rng.normal(size=(len(E), N * b))), _t(rng.normal(size=(len(E), N - 1)))
+    opt = negf.options(precision=1)
+    d = negf.Device(_t(dev.D[None]), _t(dev.T[None]), iface=(r, c))
+    Et = _t(E)
+    st = torch.zeros(len(E), dtype=torch.int32, device="cuda")
+    lead = negf.lead_selfenergy(d, Et, st, opt)
+    g0, _ = negf.rgf_adjoint(d, Et, st, lead["sigma_R"], lead["sigma_L"], opt, density_bar=cb,
+                             current_bar=db, V=V)
+    ck = negf.checkpoint_buffer(d, len(E))
+    negf.rgf_solve(d, Et, st, lead["sigma_R"], lead["sigma_L"], opt, V=V, checkpoints=ck)
+    g1, st1 = negf.rgf_adjoint(d, Et, st, lead["sigma_R"], lead["sigma_L"], opt, density_bar=cb,
+                               current_bar=db, V=V, checkpoints=ck)
+    torch.cuda.synchronize()
+    assert np.all(st1.cpu().numpy() == 0)
+    g0, g1 = g0.cpu().numpy(), g1.cpu().numpy()
+    assert np.abs(g1 - g0).max() <= 1e-12 * np.abs(g0).max()
