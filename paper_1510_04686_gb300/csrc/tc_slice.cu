@@ -232,12 +232,12 @@ __global__ void __launch_bounds__(256) k_slice(int n_lines, int K, int L, BMc<do
   }
 }
 
-// Slicing of 8 lines per CTA with the whole strip (8 lines x K complex values) held in shared
-// memory: the operand is read from memory once (the exponent pass and the digit pass both read
-// the strip), and each lane converts one complex value, so every slice store of a warp is one
-// contiguous 128-byte row segment.  Used when the strip fits (K up to kStripMaxK).
-constexpr int kStripLines = 8;
-constexpr int kStripMaxK = 858;  // 8 x (K + 1) x 16 B <= 110 KB: two CTAs per SM
+// Slicing of kStripLines lines per CTA with the whole strip (lines x K complex values) held in
+// shared memory: the operand is read from memory once (the exponent pass and the digit pass both
+// read the strip), and each lane converts one complex value, so every slice store of a warp is
+// one contiguous 128-byte row segment.  Used when the strip fits (K up to kStripMaxK).
+constexpr int kStripLines = 4;    // 4 lines: 4 x 401 x 16 B = 25 KB at K = 400, 8 CTAs per SM
+constexpr int kStripMaxK = 1717;  // 4 x (K + 1) x 16 B <= 110 KB
 template <bool kB, int BETA, int S>
 __global__ void __launch_bounds__(256) k_slice_strip(int n_lines, int K, int L, BMc<double> X,
                                                      int op, bool line_is_col,
@@ -255,8 +255,8 @@ __global__ void __launch_bounds__(256) k_slice_strip(int n_lines, int K, int L, 
   const bool conj = (op == OP_C);
   const z64 zero = mkc(0.0, 0.0);
   // load the strip along the operand's memory layout (coalesced either way): element e is
-  // (line e / K, k = e % K) for row lines and (line e % 8, k = e / 8) for column lines; eight
-  // loads per thread are in flight before their shared-memory stores
+  // (line e / K, k = e % K) for row lines and (line e % L, k = e / L) for column lines (L =
+  // kStripLines); eight loads per thread are in flight before their shared-memory stores
   const int tot = kStripLines * K;
   for (int e0 = threadIdx.x; e0 < tot; e0 += 8 * 256) {
     z64 v[8];
