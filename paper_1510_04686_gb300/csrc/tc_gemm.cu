@@ -171,19 +171,37 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
       "r"(r[15])
       : "memory");
 }
+// 8 consecutive TMEM columns of this warp's lane quarter
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                 "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(
+                   taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+               "r"(r[7])
+               : "memory");
+}
 template <int W>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t* r) {
   if constexpr (W == 32)
     tmem_ld32(taddr, r);
-  else
+  else if constexpr (W == 16)
     tmem_ld16(taddr, r);
+  else
+    tmem_ld8(taddr, r);
 }
 template <int W>
 __device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t* r) {
   if constexpr (W == 32)
     tmem_st32(taddr, r);
-  else
+  else if constexpr (W == 16)
     tmem_st16(taddr, r);
+  else
+    tmem_st8(taddr, r);
 }
 __device__ __forceinline__ void tmem_st_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -229,6 +247,56 @@ __device__ __forceinline__ z64 coef_mul(int cls, z64 a, z64 x) {
 // |x| of a double as its bit pattern without the sign (orders like |x| for finite values)
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// One accumulator group added into the running sums of this warp's TMEM lanes, columns
+// [cbase, cbase + NCH FW): the exact FP32 group value v and the unevaluated pair hi + lo
+// (TwoSum, renormalised); first = true initialises the pair (hi = v, lo = 0).  Chunk k + 1 is
+// loaded from TMEM while chunk k is summed and stored, so the load latency overlaps the adds.
+template <int FW, int NCH>
+__device__ __forceinline__ void flush_group(bool first, uint32_t tacc, uint32_t thi,
+                                            uint32_t tlo, int cbase) {
+  uint32_t v[2][FW], h[2][FW], l[2][FW];
+  tmem_ld<FW>(tacc + cbase, v[0]);
+  if (!first) {
+    tmem_ld<FW>(thi + cbase, h[0]);
+    tmem_ld<FW>(tlo + cbase, l[0]);
+  }
+#pragma unroll
+  for (int k = 0; k < NCH; ++k) {
+    const int cur = k & 1, nxt = cur ^ 1;
+    tmem_ld_wait();  // chunk k has landed (the only load in flight)
+    if (k + 1 < NCH) {
+      const uint32_t c = (uint32_t)(cbase + (k + 1) * FW);
+      tmem_ld<FW>(tacc + c, v[nxt]);
+      if (!first) {
+        tmem_ld<FW>(thi + c, h[nxt]);
+        tmem_ld<FW>(tlo + c, l[nxt]);
+      }
+    }
+    if (first) {
+#pragma unroll
+      for (int j = 0; j < FW; ++j) {
+        h[cur][j] = v[cur][j];
+        l[cur][j] = 0u;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < FW; ++j) {
+        const float hj = __uint_as_float(h[cur][j]), vj = __uint_as_float(v[cur][j]);
+        const float s1 = hj + vj;
+        const float bp = s1 - hj;
+        const float e1 = (hj - (s1 - bp)) + (vj - bp);
+        const float l1 = __uint_as_float(l[cur][j]) + e1;
+        const float h2 = s1 + l1;
+        h[cur][j] = __float_as_uint(h2);
+        l[cur][j] = __float_as_uint(l1 - (h2 - s1));
+      }
+    }
+    const uint32_t c = (uint32_t)(cbase + k * FW);
+    tmem_st<FW>(thi + c, h[cur]);
+    tmem_st<FW>(tlo + c, l[cur]);
+  }
 }
 
 __device__ __forceinline__ float warp_max_f(float v) {
@@ -328,8 +396,8 @@ __global__ void __launch_bounds__(kThreads, MINB)
   // CTAs per SM (MINB = 2) must fit the SM's 512 columns together
   constexpr uint32_t kTmemCols = NT * (kAccBufs + 2);
   static_assert(kTmemCols * MINB <= 512 && (kTmemCols & (kTmemCols - 1)) == 0, "TMEM budget");
-  // epilogue columns per TMEM load: 16 in the register-lean two-CTA form
-  constexpr int CW = MINB == 1 ? 32 : 16;
+  // columns per TMEM load of the final pass (and of the two-CTA form's flushes)
+  constexpr int CW = 16;
   static_assert((NT / 2) % CW == 0, "epilogue chunks");
   static_assert(CG == 1 || CG == 2, "one CTA or a CTA pair per MMA");
   using CF = Cfg<NT, STAGES, CG, G, KPS>;
@@ -589,6 +657,10 @@ __global__ void __launch_bounds__(kThreads, MINB)
       if (!mbar_wait(&accfull[buf], (acc / kAccBufs) & 1, abort_flag)) break;
       tc_fence_after();
       const bool last = (acc == n_exec - 1);
+      if (MINB == 1 && !last) {
+        flush_group<8, NT / 16>(acc == 0, tmem + lane_off + (uint32_t)(buf * NT), t_hi, t_lo,
+                                cbase);
+      } else {
       for (int c0 = cbase; c0 < cbase + NT / 2; c0 += CW) {
         uint32_t v[CW], h[CW], l[CW];
         tmem_ld<CW>(tmem + lane_off + (uint32_t)(buf * NT + c0), v);
@@ -656,6 +728,7 @@ __global__ void __launch_bounds__(kThreads, MINB)
             __syncwarp();
           }
         }
+      }
       }
       tmem_st_wait();
       tc_fence_before();
