@@ -32,10 +32,10 @@ WORK = dict(N=70, b=400, n_E=512, n_k=8, ge_frac=0.1, eta=1e-6, seed=1001,
 METRIC = "RGF energy-points/s (leads + forward/backward sweeps + observables + FP64 quadrature)"
 PEAKS_FALLBACK = dict(hbm_gbs=6800.0, bf16_tflops=1900.0, bf16_tflops_sustained=1700.0)
 # DRAM bytes (read + write) of k_tc_gemm per 400 x 400 x 400 complex item from an ncu capture of
-# a 64-item 48-bit launch of tensor-core configuration 18 (803.3 MB read + 149.7 MB written),
+# a 64-item 48-bit launch of tensor-core configuration 18 (820.4 MB read + 149.1 MB written),
 # scaled by the items of a launch; None once the kernel has changed since the capture (the line
 # then reports null).
-TC_DRAM_BYTES_PER_ITEM_B400 = (803.316480e6 + 149.674496e6) / 64
+TC_DRAM_BYTES_PER_ITEM_B400 = (820.392448e6 + 149.107456e6) / 64
 # configurations 18 and 19 run the same launch at b = 400 (one K part under either policy)
 TC_PROFILED_CONFIGS = (18, 19)
 GOLDEN = os.path.join(ROOT, "tests", "golden", "c1_oracle.json")

@@ -332,35 +332,38 @@ __global__ void __launch_bounds__(kThreads) k_gj_panel(int n, int k0, int w, int
 
 // Trailing update of a Gauss-Jordan panel step: C += U T for every item, with U the eliminated
 // panel (n x w, row stride nb), T the pivot rows (w x n) and w <= kMaxPanel (FP32 only: the
-// FP64 blocks would not fit the static shared memory).  A 64 x 64 block of
-// C per CTA: the whole U and T blocks are staged in shared memory at once (one barrier), and C is
-// read into the accumulators before the multiply-adds so that its latency overlaps the staging.
+// FP64 blocks would not fit the static shared memory).  An 80 x 80 block of C per CTA (n = 400
+// is 5 x 5 blocks with no padding; 64 x 64 blocks would pad it to 448^2, 25 % more work), each
+// thread 5 x 5 complex accumulators: rows ty + 16 i, columns tx + 16 j.  The whole U and T blocks
+// are staged in shared memory at once (one barrier), and C is read into the accumulators before
+// the multiply-adds so that its latency overlaps the staging.
 constexpr int kMaxPanel = 32;
+constexpr int kUpdTile = 80;
 template <typename R>
 __global__ void __launch_bounds__(256) k_gj_update(int n, int w, int nb, const cx<R>* U,
                                                    const cx<R>* T, BM<R> C,
                                                    const int32_t* active) {
   const int p = blockIdx.z;
   if (active && !active[p]) return;
-  __shared__ cx<R> Us[kMaxPanel][65];  // padded: the staging writes walk down a column
-  __shared__ cx<R> Ts[kMaxPanel][64];
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  __shared__ cx<R> Us[kUpdTile][kMaxPanel + 1];  // row-major like U; padded rows
+  __shared__ cx<R> Ts[kMaxPanel][kUpdTile];
+  const int m0 = blockIdx.y * kUpdTile, n0 = blockIdx.x * kUpdTile;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const cx<R>* u = U + (long long)p * n * nb;
   const cx<R>* t = T + (long long)p * nb * n;
   cx<R>* c = bat(C, p);
   const cx<R> zero = mkc<R>(R(0), R(0));
-  cx<R> acc[4][4];
+  cx<R> acc[5][5];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 5; ++j) {
       const int r = m0 + ty + 16 * i, col = n0 + tx + 16 * j;
       acc[i][j] = (r < n && col < n) ? c[(long long)r * C.ld + col] : zero;
     }
-  // staging: slot e of U is (row e / 32, column e % 32), of T (row e / 64, column e % 64); all
+  // staging: slot e of U is (row e / 32, column e % 32), of T (row e / 80, column e % 80); all
   // loads are issued before the first shared-memory store
-  constexpr int kPer = kMaxPanel * 64 / 256;
+  constexpr int kPer = kMaxPanel * kUpdTile / 256;  // 10
   cx<R> us[kPer], ts[kPer];
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
@@ -371,31 +374,31 @@ __global__ void __launch_bounds__(256) k_gj_update(int n, int w, int nb, const c
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
     const int e = threadIdx.x + 256 * q;
-    const int k = e >> 6, col = e & 63;
+    const int k = e / kUpdTile, col = e % kUpdTile;
     ts[q] = (k < w && n0 + col < n) ? t[(long long)k * n + n0 + col] : zero;
   }
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
     const int e = threadIdx.x + 256 * q;
-    Us[e & 31][e >> 5] = us[q];
-    Ts[e >> 6][e & 63] = ts[q];
+    Us[e >> 5][e & 31] = us[q];
+    Ts[e / kUpdTile][e % kUpdTile] = ts[q];
   }
   __syncthreads();
   for (int k = 0; k < w; ++k) {
-    cx<R> av[4], bv[4];
+    cx<R> av[5], bv[5];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) av[i] = Us[k][ty + 16 * i];
+    for (int i = 0; i < 5; ++i) av[i] = Us[ty + 16 * i][k];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) bv[j] = Ts[k][tx + 16 * j];
+    for (int j = 0; j < 5; ++j) bv[j] = Ts[k][tx + 16 * j];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 5; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) cfma(acc[i][j], av[i], bv[j]);
+      for (int j = 0; j < 5; ++j) cfma(acc[i][j], av[i], bv[j]);
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 5; ++j) {
       const int r = m0 + ty + 16 * i, col = n0 + tx + 16 * j;
       if (r < n && col < n) c[(long long)r * C.ld + col] = acc[i][j];
     }
@@ -486,8 +489,8 @@ cudaError_t gj_inverse(cudaStream_t s, int P, int n, BM<R> M, BM<R> X, cx<R>* U,
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if constexpr (std::is_same<R, float>::value) {
       // FP32: panels are at most kMaxPanel wide (gj_panel_width); FP64 is FMA-bound either way
-      k_gj_update<R><<<dim3((n + 63) / 64, (n + 63) / 64, P), 256, 0, s>>>(n, w, nb, U, T, M,
-                                                                         active);
+      k_gj_update<R><<<dim3((n + kUpdTile - 1) / kUpdTile, (n + kUpdTile - 1) / kUpdTile, P),
+                       256, 0, s>>>(n, w, nb, U, T, M, active);
       count_launch();
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else {
