@@ -584,3 +584,46 @@ def test_trapezoid_weights_integrate_lines_exactly_on_any_mesh():
     w = O.trapezoid_weights(E)
     assert abs(w.sum() - (E[-1] - E[0])) < 1e-14
     assert abs((w * (2.0 * E + 1.0)).sum() - ((E[-1] ** 2 + E[-1]) - (E[0] ** 2 + E[0]))) < 1e-13
+
+
+def _decimate(h, alpha, z, perturb_at=0, rel=1e-14, seed=0, max_iter=100, tol=1e-13):
+    """The decimation of oracle.sancho_rubio with g perturbed by rel * max|g| (complex Gaussian)
+    at one doubling step; returns the surface Green's function and the steps run."""
+    rng = np.random.default_rng(seed)
+    b = h.shape[0]
+    I = np.eye(b)
+    eps_s, eps = h.astype(complex).copy(), h.astype(complex).copy()
+    a, be = alpha.astype(complex).copy(), alpha.conj().T.astype(complex).copy()
+    scale = max(np.abs(h).max(), np.abs(alpha).max())
+    for it in range(1, max_iter + 1):
+        g = np.linalg.inv(z * I - eps)
+        if it == perturb_at:
+            g = g + rel * np.abs(g).max() * (rng.standard_normal(g.shape)
+                                             + 1j * rng.standard_normal(g.shape))
+        agb, bga = a @ g @ be, be @ g @ a
+        eps_s, eps = eps_s + agb, eps + agb + bga
+        a, be = a @ g @ a, be @ g @ be
+        if max(np.abs(a).max(), np.abs(be).max()) < tol * scale:
+            break
+    return np.linalg.inv(z * I - eps_s), it
+
+
+def test_late_decimation_steps_barely_propagate_rounding():
+    """The premise of the mixed form's lead precision schedule (fewer bits in later doubling
+    steps): on a device other than the one the schedule was measured on, a 1e-14 perturbation of
+    g at any step from the 15th on moves Sigma by far less than the 1e-6 accuracy target, while
+    the unperturbed loop is the oracle's decimation."""
+    dev = make_device(6, 12, 5151, ge_frac=0.2)
+    h, t = dev.D[-1], dev.T[-1]
+    worst_late = 0.0
+    for E in (-1.9, -0.7, -0.05, 0.4, 1.3, 2.2):
+        z = E + 1e-6j
+        g0, n = _decimate(h, t, z)
+        ref, n_ref, ok = O.sancho_rubio(h, t, z)
+        assert ok and n == n_ref and np.abs(g0 - ref).max() <= 1e-12 * np.abs(ref).max()
+        s0 = t @ g0 @ t.conj().T
+        for step in range(15, n + 1):
+            g1, _ = _decimate(h, t, z, perturb_at=step, seed=step)
+            s1 = t @ g1 @ t.conj().T
+            worst_late = max(worst_late, np.abs(s1 - s0).max() / np.abs(s0).max())
+    assert worst_late < 1e-9
