@@ -221,9 +221,19 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "c128", "data": "synthetic",
         "config": {"workload": WORK["name"], "points_per_step": 1},
         "cpu_baseline": {"value": v, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "blas": _blas_info(), "host_cores": os.cpu_count(),
                          "sample": f"{args.steps} points of the workload, one per step"},
         "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def _blas_info():
+    """numpy's BLAS (name and version) for the CPU-baseline record."""
+    try:
+        d = np.show_config(mode="dicts")["Build Dependencies"]["blas"]
+        return f"{d.get('name', '?')} {d.get('version', '')}".strip()
+    except Exception:
+        return "unknown"
 
 
 def _blas_threads():
@@ -675,7 +685,7 @@ def extras(args, negf, torch, device, dvc, Hd, dev_np, E, wE, wk, prec):
     refs = [O.solve_point(Hd[kk[i]], dev_np.T, E[ee[i]], WORK["eta"], None) for i in range(cp)]
     dt = time.perf_counter() - t0
     out["cpu_baseline"] = {"value": cp / dt, "unit": "points/s", "cores": _blas_threads(),
-                           "kind": "oracle",
+                           "kind": "oracle", "blas": _blas_info(), "host_cores": os.cpu_count(),
                            "sample": f"{cp} (E,k) points of the workload, numpy complex128"}
 
     def rel(a, b):
