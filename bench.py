@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the CPU-oracle, FP64-GPU and end-to-end side measurements")
     ap.add_argument("--workload", default="rgf",
-                    choices=["rgf", "scba", "adjoint", "ragged", "gemm", "iface"],
+                    choices=["rgf", "scba", "adjoint", "ragged", "gemm", "iface", "zinv"],
                     help="rgf: the throughput line above; scba / adjoint / ragged / gemm: side "
                          "measurements of the Born loop (N=70, b=600), the adjoint sweep "
                          "(b=3430), ragged block sizes (b=200..800) and the batched tensor-core "
@@ -413,6 +413,26 @@ def run_side(args):
                             "speedup_vs_dense": it["step"] / dn_["step"],
                             "max_density_difference_vs_dense": dn,
                             "max_sigma_difference_vs_dense": ds})
+    elif args.workload == "zinv":
+        # the mixed block inverse alone (FP32 Gauss-Jordan start + Newton-Schulz refinement)
+        b, nb = args.gemm_b, args.gemm_batch
+        g = torch.Generator(device=dvc).manual_seed(2)
+        M0 = torch.randn((nb, b, b), dtype=torch.complex128, device=dvc, generator=g) / b ** 0.5
+        M0 += 4.0 * torch.eye(b, dtype=torch.complex128, device=dvc)
+        M = torch.empty_like(M0)
+
+        def inv():
+            M.copy_(M0)  # the inverse consumes its input
+            return negf.zinv(M, precision=negf.PREC_MIXED)
+        ms, (X, st) = _timed(torch, inv, args.warmup, args.steps)
+        res = (torch.eye(b, dtype=torch.complex128, device=dvc) - M0 @ X).abs().max().item()
+        line.update(metric="batched block inverses/s (mixed: FP32 Gauss-Jordan + Newton-Schulz)",
+                    value=nb * args.steps / (ms / 1e3), unit="inverses/s",
+                    ms_per_step=ms / args.steps, dtype="fp32 elimination, bf16-slices->fp32 "
+                    "refinement (fp64 in/out)",
+                    config={"workload": f"{nb} items of {b} x {b} complex128",
+                            "max_residual": res,
+                            "status_ok": bool((st == 0).all().item())})
     elif args.workload == "gemm":
         b, nb = args.gemm_b, args.gemm_batch
         if args.tc_config is not None:
