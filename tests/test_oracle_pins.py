@@ -627,3 +627,29 @@ def test_late_decimation_steps_barely_propagate_rounding():
             s1 = t @ g1 @ t.conj().T
             worst_late = max(worst_late, np.abs(s1 - s0).max() / np.abs(s0).max())
     assert worst_late < 1e-9
+
+
+def test_decimation_keeps_the_interface_support():
+    """The premise of the interface-coupling decimation: with a hopping supported on its last r
+    rows R and first c columns C, every doubling step keeps alpha_n on C x R and beta_n on
+    R x C for the left lead (alpha_0 = tau^H), and the surface self-energy lives on C x C."""
+    N, b, r, c = 4, 10, 3, 4
+    dev = make_device(N, b, 808, iface=(r, c))
+    t = dev.T[0]
+    assert np.all(t[:b - r, :] == 0) and np.all(t[:, c:] == 0)
+    R, C = np.arange(b - r, b), np.arange(c)
+    h = dev.D[0]
+    z = 0.3 + 1e-6j
+    I = np.eye(b)
+    eps_s, eps = h.astype(complex).copy(), h.astype(complex).copy()
+    a, be = t.conj().T.astype(complex), t.astype(complex)
+    outside_a = np.ones((b, b), bool)
+    outside_a[np.ix_(C, R)] = False
+    for _ in range(12):
+        g = np.linalg.inv(z * I - eps)
+        agb, bga = a @ g @ be, be @ g @ a
+        eps_s, eps = eps_s + agb, eps + agb + bga
+        a, be = a @ g @ a, be @ g @ be
+        assert np.all(a[outside_a] == 0) and np.all(be[outside_a.T] == 0)
+    sig = O.lead_self_energies(dev.D, dev.T, 0.3, 1e-6, 0.1, -0.1, KT)["sigL"]
+    assert np.all(sig[c:, :] == 0) and np.all(sig[:, c:] == 0)
