@@ -55,7 +55,8 @@ def test_mixed_rgf_matches_oracle(N, b):
 
 
 def test_mixed_config0_integrated_parity():
-    """configs[0] in the mixed form: integrated density and current within 1e-6 of the oracle."""
+    """The small ballistic workload (N = 20 slabs x 40 x 40 blocks, 64 energies) in the mixed
+    form: integrated density and current within 1e-6 of the oracle."""
     w = config_workload(0)
     dev = w["device"]
     E, wE = w["E"], w["wE"]

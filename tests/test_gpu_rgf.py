@@ -186,7 +186,8 @@ def test_decimation_cap_reports_not_converged():
 
 
 def test_config0_integrated_parity():
-    """configs[0]: N = 20, b = 40, 64 energies in [-3, 3], eta = 1e-6, one k-point."""
+    """The small ballistic workload: N = 20, b = 40, 64 energies in [-3, 3], eta = 1e-6, one
+    k-point."""
     w = config_workload(0)
     dev = w["device"]
     E, wE = w["E"], w["wE"]
