@@ -227,6 +227,37 @@ def run_reference(args):
     }), flush=True)
 
 
+_ONE_CORE = r"""
+import sys, time
+sys.path.insert(0, {root!r})
+import oracle as O
+from workloads import make_device, hamiltonian_k, k_grid, energy_grid_linspace
+dev = make_device({N}, {b}, {seed}, ge_frac={ge}, with_k=True)
+ks, _ = k_grid({n_k})
+Hd = hamiltonian_k(dev, float(ks[{k}]))[0]
+E, _ = energy_grid_linspace(-3.0, 3.0, {n_E})
+t0 = time.perf_counter()
+O.solve_point(Hd, dev.T, E[{e}], {eta}, None)
+print(time.perf_counter() - t0)
+"""
+
+
+def _oracle_one_core(k, e):
+    """Seconds of one oracle point of the workload with BLAS on one thread (a child process,
+    so that the thread count is fixed before numpy loads); None if it could not run."""
+    code = _ONE_CORE.format(root=ROOT, N=WORK["N"], b=WORK["b"], seed=WORK["seed"],
+                            ge=WORK["ge_frac"], n_k=WORK["n_k"], k=int(k), n_E=WORK["n_E"],
+                            e=int(e), eta=WORK["eta"])
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=600)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except Exception:
+        return None
+
+
 def _blas_info():
     """numpy's BLAS (name and version) for the CPU-baseline record."""
     try:
@@ -707,6 +738,11 @@ def extras(args, negf, torch, device, dvc, Hd, dev_np, E, wE, wk, prec):
     out["cpu_baseline"] = {"value": cp / dt, "unit": "points/s", "cores": _blas_threads(),
                            "kind": "oracle", "blas": _blas_info(), "host_cores": os.cpu_count(),
                            "sample": f"{cp} (E,k) points of the workload, numpy complex128"}
+    t1 = _oracle_one_core(kk[0], ee[0])
+    if t1:
+        out["cpu_baseline"]["single_core"] = {"value": 1.0 / t1, "unit": "points/s", "cores": 1,
+                                              "sample": "the first of those points, BLAS on one "
+                                                        "thread"}
 
     def rel(a, b):
         return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
