@@ -23,8 +23,9 @@
  *    "host".  The library never frees or keeps caller memory after a call returns.
  *  - Temporary device memory is the caller's workspace (`ws`, `ws_bytes`), sized by
  *    negf_workspace_size().  The library allocates no device memory of its own, apart from
- *    two fixed device arrays reserved on every GPU that loads it: the 32 MiB scratch of
- *    negf_zinv_batched_noalloc and an 8-byte diagnostic counter.
+ *    fixed device arrays reserved on every GPU that loads it: the 32 MiB scratch of
+ *    negf_zinv_batched_noalloc and a few bytes of diagnostic counters (FP64 fallbacks,
+ *    profiled flops).
  *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
  *    Outputs are valid after the stream is synchronised.  Several points are solved
  *    concurrently; the workspace holds a chunk of them at a time.
